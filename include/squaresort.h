@@ -1,0 +1,197 @@
+/*
+ * squaresort.h -- C ABI of the GB300 SquareSort library (libsquaresort.so).
+ *
+ * SquareSort (Koucky & Matejka, "SquareSort: a cache-oblivious sorting
+ * algorithm", arXiv 2407.14801) views n items as m = ceil(sqrt(n)) columns of
+ * at most m items, sorts every column, picks m-1 random pivots, moves the
+ * items bucket by bucket with a SkewTranspose and sorts every bucket,
+ * recursing wherever a column or bucket is larger than the leaf cutoff
+ * (Section 2, Algorithm 1).
+ *
+ * Conventions for every call below:
+ *  - Pointers are plain addresses.  Key and payload buffers may be device
+ *    memory (the fast path) or, for sq_sort / sq_sort_ex only, host memory,
+ *    which is staged through device memory inside the call.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Device
+ *    work is ordered on it; calls return after the work is finished (the
+ *    engine reads per-round work counts back to the host).
+ *  - Element order: (key, val) pairs by (ordinal(key), val).  ordinal is the
+ *    identity for SQ_U32 / SQ_U64; SQ_F32 keys are IEEE-754 binary32 bit
+ *    patterns ordered -inf < ... < -0 < +0 < ... < +inf < NaN, every NaN equal
+ *    (ties among NaNs broken by val); the bits of every key are preserved.
+ *  - Errors are returned as sq_status, never thrown; sq_last_error() gives a
+ *    thread-local message for the last failing call of the calling thread.
+ */
+#ifndef SQUARESORT_H
+#define SQUARESORT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void *sq_stream_t; /* a cudaStream_t */
+
+typedef enum { SQ_U32 = 0, SQ_U64 = 1, SQ_F32 = 2 } sq_dtype;
+
+typedef enum {
+  SQ_OK = 0,
+  SQ_ERR_INVALID = 1,  /* bad argument (null pointer, size, dtype, cutoff) */
+  SQ_ERR_NOMEM = 2,    /* device memory or an internal work list ran out */
+  SQ_ERR_BUDGET = 3,   /* a request does not fit the server's HBM budget */
+  SQ_ERR_TIMEOUT = 4,  /* a bounded wait ran out */
+  SQ_ERR_CUDA = 5,     /* a CUDA runtime call failed */
+  SQ_PENDING = 6,      /* sq_serve_poll: not finished yet */
+  SQ_ERR_ATTEMPTS = 7, /* no acceptable pivot sample in 256 draws (e.g. repeated (key, val) pairs) */
+  SQ_ERR_INTERNAL = 8  /* an engine invariant failed */
+} sq_status;
+
+/* Sort n (key, val) pairs in place (Algorithm 1, Section 2.1).
+ *  keys : n keys of `dtype` (4 bytes for SQ_U32/SQ_F32, 8 for SQ_U64).
+ *  vals : n uint32 payloads moved with their keys; ties between equal keys
+ *         are broken by val, so with distinct vals the result is unique.
+ *         NULL: the original position is used for ties and nothing is
+ *         returned.
+ *  n    : 0 <= n <= sq_max_n(dtype).
+ *  seed : seeds the pivot draws; the result does not depend on it, the
+ *         recursion (which pivots, how many redraws) does.
+ * Scratch of n*(key bytes + 4) plus O(n/16) bytes of metadata comes from the
+ * CUDA stream-ordered allocator and is released before return. */
+sq_status sq_sort(void *keys, uint32_t *vals, uint64_t n, sq_dtype dtype, uint64_t seed, sq_stream_t stream);
+
+/* Per-node record of a traced sort: one per SquareSort call with n > cutoff,
+ * written when its pivots are accepted (Algorithm 1, pivot step). */
+typedef struct {
+  uint64_t off;      /* first element of the node in the array */
+  uint64_t n;        /* node size */
+  uint64_t m;        /* ceil(sqrt(n)): columns = buckets */
+  uint64_t hash;     /* path hash that seeds its pivot draws */
+  uint32_t depth;    /* root = 0 */
+  uint32_t kind;     /* 0 root, 1 column child, 2 bucket child */
+  uint32_t attempts; /* pivot samples drawn (1 = first accepted) */
+  uint32_t index;    /* column / bucket index within the parent */
+} sq_trace_rec;
+
+typedef struct {
+  uint32_t cutoff;        /* leaf iff n <= cutoff; 0 = tuned default; 2..sq_max_leaf(dtype) */
+  uint32_t trace_cap;     /* capacity of `trace` in records (0 = no trace) */
+  sq_trace_rec *trace;    /* host array receiving node records (any order) */
+  uint32_t *trace_count;  /* out: records produced (may exceed trace_cap) */
+} sq_sort_opts;
+
+/* sq_sort with an explicit leaf cutoff and an optional recursion trace.
+ * opts may be NULL (= sq_sort). */
+sq_status sq_sort_ex(void *keys, uint32_t *vals, uint64_t n, sq_dtype dtype, uint64_t seed, sq_stream_t stream,
+                     const sq_sort_opts *opts);
+
+/* Stand-alone SkewTranspose (Section 2.2, Algorithms 2 and 3).
+ * keys_in/vals_in hold `cols` columns, column i = elements
+ * [min(i*rows, n), min((i+1)*rows, n)), each sorted by the element order.
+ * The k-1 sorted pivots (pivot_keys/pivot_vals, device) define k buckets,
+ * bucket j = { e : p_{j-1} <= e < p_j } with p_0 = -inf, p_k = +inf.  The
+ * call writes to keys_out/vals_out every bucket in turn, each holding its
+ * elements column by column and, within a column, in sorted order; and
+ * writes the k+1 bucket starts (uint64, device) to bucket_start_out.
+ * All buffers are caller-owned device memory; in and out must not overlap. */
+typedef struct {
+  sq_dtype dtype;
+  uint64_t n;
+  const void *keys_in;
+  const uint32_t *vals_in;
+  void *keys_out;
+  uint32_t *vals_out;
+  const void *pivot_keys;
+  const uint32_t *pivot_vals;
+  uint64_t k;                  /* buckets; 1 <= k <= sq_max_leaf(dtype) + 1 */
+  uint64_t *bucket_start_out;  /* k+1 entries */
+} sq_skew_buf;
+
+/* rows >= 1, cols >= 1, n <= rows*cols, n < 2^32. */
+sq_status sq_skew_transpose(const sq_skew_buf *buf, uint64_t rows, uint64_t cols, sq_stream_t stream);
+
+/* One instance of a batched sort: device buffers, sorted in place. */
+typedef struct {
+  void *keys;
+  uint32_t *vals; /* NULL allowed, as in sq_sort */
+  uint64_t n;
+  sq_dtype dtype;
+  uint64_t seed;
+} sq_sort_desc;
+
+/* Sort `count` independent instances of any sizes and key types together:
+ * every recursion round of every instance runs in the same kernel launches
+ * (work items pulled from device lists), instead of one launch sequence per
+ * instance.  Each instance's result equals sq_sort of that instance. */
+sq_status sq_sort_batch(const sq_sort_desc *descs, uint32_t count, sq_stream_t stream);
+
+/* ------------------------------------------------------------- serving --- */
+
+typedef struct sq_server sq_server;
+
+typedef struct {
+  uint32_t max_inflight;  /* requests admitted at once (0 = 4096) */
+  uint32_t cutoff;        /* leaf cutoff (0 = tuned default) */
+  int device;             /* CUDA device ordinal */
+} sq_serve_opts;
+
+/* Create a server whose device memory pool holds at most hbm_budget_bytes
+ * (requests' keys, vals and scratch).  A background thread admits queued
+ * requests while the pool and the in-flight limit allow, and runs every
+ * admitted request's recursion rounds together with the requests already
+ * on the GPU (continuous batching).  opts may be NULL. */
+sq_status sq_serve_create(sq_server **out, uint64_t hbm_budget_bytes, const sq_serve_opts *opts);
+
+/* Queue one sort.  desc->keys / desc->vals are HOST pointers that must stay
+ * valid until sq_serve_poll reports completion; the result is written back
+ * to them.  A request larger than the whole budget fails with
+ * SQ_ERR_BUDGET.  *ticket identifies the request. */
+sq_status sq_serve_submit(sq_server *srv, const sq_sort_desc *desc, uint64_t *ticket);
+
+/* SQ_PENDING while the request runs; SQ_OK once its result is in the
+ * caller's buffers (then *result holds the request's own status and
+ * *latency_s the time from submit to completion).  Polling a finished ticket
+ * again returns SQ_ERR_INVALID. */
+sq_status sq_serve_poll(sq_server *srv, uint64_t ticket, sq_status *result, double *latency_s);
+
+/* Stop the server after draining admitted work; frees the pool. */
+sq_status sq_serve_destroy(sq_server *srv);
+
+/* ----------------------------------------------------------- utilities --- */
+
+/* Message of the calling thread's last failing call ("" if none). */
+const char *sq_last_error(void);
+
+/* Largest n accepted by sq_sort for `dtype` ((max leaf + 1)^2). */
+uint64_t sq_max_n(sq_dtype dtype);
+
+/* Largest leaf (and pivot sample) sorted by one thread group. */
+uint32_t sq_max_leaf(sq_dtype dtype);
+
+/* Default leaf cutoff for `dtype` (0 restores the built-in default). */
+sq_status sq_set_cutoff(sq_dtype dtype, uint32_t cutoff);
+uint32_t sq_get_cutoff(sq_dtype dtype);
+
+/* Per-kernel-family counters accumulated by all calls of this process.
+ * Families: 0 leaf sort, 1 plan, 2 pivots, 3 count, 4 prefix scan,
+ * 5 bucket starts, 6 SkewTranspose, 7 child expansion, 8 auxiliary. */
+typedef struct {
+  uint64_t launches[9];
+  double ms[9];     /* summed kernel durations (only while profiling is on) */
+  double bytes[9];  /* algorithmic bytes: leaf 2(w+4)/elem, count (w+4)/elem, skew 2(w+4)/elem */
+  uint64_t rounds;  /* recursion rounds (one host read-back each) */
+  uint64_t nodes;   /* SquareSort calls with n > cutoff */
+  uint64_t sorts;   /* instances sorted */
+} sq_stats;
+
+void sq_stats_get(sq_stats *out);
+void sq_stats_reset(void);
+/* on != 0: time every launch with CUDA events on its stream (adds a little
+ * host work per launch). */
+void sq_set_profiling(int on);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SQUARESORT_H */

@@ -1,0 +1,538 @@
+// Host driver of the SquareSort engine: plans scratch memory, seeds the roots
+// and runs rounds of kernels until every instance is sorted.  Included once
+// per key type (sq_engine_<type>.cu).
+#pragma once
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "sq_engine.h"
+#include "sq_kernels.cuh"
+
+namespace sq {
+
+// ------------------------------------------------------------ statistics ---
+struct StatsBox {
+  std::mutex mu;
+  EngineStats s{};
+  std::atomic<int> profiling{0};
+};
+StatsBox &stats_box();
+
+#define SQ_CU(call)                                                                   \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      snprintf(err, errlen, "%s failed: %s", #call, cudaGetErrorString(e_));         \
+      return 5; /* SQ_ERR_CUDA */                                                     \
+    }                                                                                 \
+  } while (0)
+
+template <int DT>
+struct Engine {
+  typedef KT<DT> K;
+  typedef typename K::elem_t E;
+  static constexpr int NCLASS = LeafCfg<DT>::nclass;
+  static constexpr int SKEW_CAP = sizeof(E) == 8 ? 4096 : 2048;
+  static constexpr size_t KEY_BYTES = sizeof(typename K::key_t);
+
+  static u32 max_leaf() { return class_cap(NCLASS - 1); }
+
+  // ---- launch helpers ---------------------------------------------------
+  struct Launcher {
+    cudaStream_t st;
+    bool prof;
+    EngineStats local{};
+    std::vector<cudaEvent_t> evs;
+    std::vector<int> fam;
+    void begin(int f) {
+      local.launches[f]++;
+      if (prof) {
+        cudaEvent_t a;
+        cudaEventCreate(&a);
+        cudaEventRecord(a, st);
+        evs.push_back(a);
+        fam.push_back(f);
+      }
+    }
+    void end() {
+      if (prof) {
+        cudaEvent_t b;
+        cudaEventCreate(&b);
+        cudaEventRecord(b, st);
+        evs.push_back(b);
+      }
+    }
+    void collect() {  // after a stream synchronize
+      for (size_t i = 0; i + 1 < evs.size(); i += 2) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, evs[i], evs[i + 1]);
+        local.ms[fam[i / 2]] += ms;
+        cudaEventDestroy(evs[i]);
+        cudaEventDestroy(evs[i + 1]);
+      }
+      evs.clear();
+      fam.clear();
+    }
+  };
+
+  template <class Kern>
+  static cudaError_t set_smem(Kern kern, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  }
+
+  template <int T, int R, bool WARP>
+  static cudaError_t launch_leaf(Launcher &L, const Ctx &c, int cls, u32 count) {
+    typedef Sorter<K, T, R, WARP> S;
+    const size_t smem = (size_t)(WARP ? 8 : 1) * S::SMEM * sizeof(E);
+    auto kern = k_leaf<DT, T, R, WARP>;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    const u32 grid = WARP ? (count + 7) / 8 : count;
+    L.begin(KF_LEAF);
+    kern<<<grid, WARP ? 256 : T, smem, L.st>>>(c, cls, count);
+    L.end();
+    return cudaGetLastError();
+  }
+
+  static cudaError_t launch_leaf_class(Launcher &L, const Ctx &c, int cls, u32 count) {
+    switch (cls) {
+      case 0: return launch_leaf<32, 2, true>(L, c, 0, count);
+      case 1: return launch_leaf<32, 16, true>(L, c, 1, count);
+      case 2: return launch_leaf<128, 16, false>(L, c, 2, count);
+      case 3: return launch_leaf<512, 16, false>(L, c, 3, count);
+      default:
+        if constexpr (NCLASS > 4) return launch_leaf<1024, 16, false>(L, c, 4, count);
+        return cudaErrorInvalidValue;
+    }
+  }
+
+  template <int T, int R, bool WARP>
+  static cudaError_t launch_pivots(Launcher &L, const Ctx &c, u32 ready, u32 pmin, u32 pmax) {
+    typedef Sorter<K, T, R, WARP> S;
+    const size_t smem = (size_t)(WARP ? 8 : 1) * S::SMEM * sizeof(E);
+    auto kern = k_pivots<DT, T, R, WARP>;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    const u32 grid = WARP ? (ready + 7) / 8 : ready;
+    L.begin(KF_PIVOTS);
+    kern<<<grid, WARP ? 256 : T, smem, L.st>>>(c, ready, pmin, pmax);
+    L.end();
+    return cudaGetLastError();
+  }
+
+  static cudaError_t launch_all_pivots(Launcher &L, const Ctx &c, u32 ready, u32 max_k) {
+    cudaError_t e = cudaSuccess;
+    const u32 maxp = max_k ? max_k - 1 : 0;
+    e = launch_pivots<32, 16, true>(L, c, ready, 0, 512);
+    if (e == cudaSuccess && maxp > 512) e = launch_pivots<128, 16, false>(L, c, ready, 512, 2048);
+    if (e == cudaSuccess && maxp > 2048) e = launch_pivots<512, 16, false>(L, c, ready, 2048, 8192);
+    if constexpr (NCLASS > 4)
+      if (e == cudaSuccess && maxp > 8192) e = launch_pivots<1024, 16, false>(L, c, ready, 8192, 16384);
+    return e;
+  }
+
+  // ---- scratch plan: list capacities (proven bounds) and slab layout ------
+  struct Plan {
+    u32 leaf_cap[kLeafClasses];
+    u64 ready_cap, fresh_cap, node_cap, meta_cap;
+    size_t o_inst, o_leaves[2][kLeafClasses], o_ready[2], o_fresh[2], o_cnt, o_status, o_meta, o_done, o_trace;
+    size_t slab_bytes;
+  };
+
+  // Leaves made in one round cover disjoint ranges and come from the columns
+  // or buckets of nodes with n > cutoff (at most 2*ceil(sqrt n) each), so a
+  // round makes at most 2*(N/floor(sqrt c) + N/c) of them; ready nodes
+  // (n > c, disjoint) number at most N/(c+1), new nodes twice that.
+  static Plan make_plan(u64 total_n, u32 ninst, u32 cutoff, u32 trace_cap, int skew_only, u32 k, u32 cols) {
+    Plan P;
+    const double sc = std::floor(std::sqrt((double)cutoff));
+    const u64 leaf_bound = (u64)(2.0 * ((double)total_n / sc + (double)total_n / cutoff)) + 2ull * ninst + 64;
+    for (int c = 0; c < kLeafClasses; c++) {
+      const u64 lo = c == 0 ? 1 : (u64)class_cap(c - 1) + 1;
+      u64 cap = std::min<u64>(leaf_bound, total_n / lo + ninst + 64);
+      if (lo > cutoff || c >= NCLASS) cap = 0;  // no leaf of this class can exist
+      P.leaf_cap[c] = (u32)std::min<u64>(cap, 0xffffffffull);
+    }
+    P.ready_cap = total_n / (cutoff + 1) + ninst + 64;
+    P.fresh_cap = 2 * (total_n / (cutoff + 1)) + ninst + 64;
+    P.node_cap = std::max<u64>(1024, 2 * P.fresh_cap + ninst);
+    const double kw = (double)K::key_words;
+    P.meta_cap = (u64)((double)total_n * (1.0 / kCountCols + 1.0 / kSkewBkts) +
+                       (6.0 + kw) * ((double)total_n / std::sqrt((double)cutoff + 1) + P.ready_cap)) +
+                 32 * P.ready_cap + 4096;
+    if (skew_only) {
+      P.node_cap = 1;
+      P.ready_cap = P.fresh_cap = 1;
+      P.meta_cap = meta_layout(k, cols, (cols + kCountCols - 1) / kCountCols, (k + kSkewBkts - 1) / kSkewBkts,
+                               K::key_words)
+                       .total +
+                   64;
+    }
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+      const size_t o = off;
+      off += (bytes + 255) & ~(size_t)255;
+      return o;
+    };
+    P.o_inst = carve(sizeof(Inst) * std::max<u32>(ninst, 1));
+    for (int q = 0; q < 2; q++)
+      for (int c = 0; c < kLeafClasses; c++) P.o_leaves[q][c] = carve(sizeof(Leaf) * (size_t)P.leaf_cap[c]);
+    P.o_ready[0] = carve(4 * P.ready_cap);
+    P.o_ready[1] = carve(4 * P.ready_cap);
+    P.o_fresh[0] = carve(4 * P.fresh_cap);
+    P.o_fresh[1] = carve(4 * P.fresh_cap);
+    P.o_cnt = carve(2 * sizeof(Counters));
+    P.o_status = carve(sizeof(Status));
+    P.o_meta = carve(4 * P.meta_cap);
+    P.o_done = carve(4 * (size_t)std::max<u32>(ninst, 1));
+    P.o_trace = carve(sizeof(TraceRec) * (size_t)trace_cap);
+    P.slab_bytes = off;
+    return P;
+  }
+
+  static u64 scratch_bytes(u64 total_n, u32 ninst, u32 cutoff) {
+    const Plan P = make_plan(total_n, ninst, cutoff, 0, 0, 0, 0);
+    return P.slab_bytes + sizeof(Node) * P.node_cap + 4096;
+  }
+
+  // ---- one run ------------------------------------------------------------
+  static int run(const RunSpec &spec, cudaStream_t st, char *err, size_t errlen) {
+    const u32 ninst = spec.ninst;
+    const u32 cutoff = spec.cutoff;
+    if (cutoff < 2 || cutoff > max_leaf()) {
+      snprintf(err, errlen, "cutoff %u outside [2, %u]", cutoff, max_leaf());
+      return 1;
+    }
+    int dev = 0, nsm = 0;
+    SQ_CU(cudaGetDevice(&dev));
+    SQ_CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+
+    // ---- sizes
+    u64 total_n = 0, max_n = 0;
+    for (u32 i = 0; i < ninst; i++) {
+      total_n += spec.inst[i].n;
+      max_n = std::max<u64>(max_n, spec.inst[i].n);
+    }
+    const u64 lim = (u64)(max_leaf() + 1) * (max_leaf() + 1);
+    if (!spec.skew_only && max_n > lim) {
+      snprintf(err, errlen, "n = %llu exceeds the largest supported size %llu for this key type",
+               (unsigned long long)max_n, (unsigned long long)lim);
+      return 1;
+    }
+    const Plan P = make_plan(total_n, ninst, cutoff, spec.trace_cap, spec.skew_only, (u32)spec.k, (u32)spec.cols);
+    u32 leaf_cap[kLeafClasses];
+    for (int cl = 0; cl < kLeafClasses; cl++) leaf_cap[cl] = P.leaf_cap[cl];
+    const u64 ready_cap = P.ready_cap, fresh_cap = P.fresh_cap, meta_cap = P.meta_cap;
+    u64 node_cap = P.node_cap;
+    const size_t off = P.slab_bytes, o_inst = P.o_inst, o_ready[2] = {P.o_ready[0], P.o_ready[1]};
+    const size_t o_fresh[2] = {P.o_fresh[0], P.o_fresh[1]}, o_cnt = P.o_cnt, o_status = P.o_status;
+    const size_t o_meta = P.o_meta, o_done = P.o_done, o_trace = P.o_trace;
+    size_t o_leaves[2][kLeafClasses];
+    for (int q = 0; q < 2; q++)
+      for (int cl = 0; cl < kLeafClasses; cl++) o_leaves[q][cl] = P.o_leaves[q][cl];
+    char *slab = nullptr;
+    Node *nodes = nullptr;
+    auto dalloc = [&](void **p, size_t bytes) -> cudaError_t {
+      if (spec.dev_alloc) {
+        *p = spec.dev_alloc(spec.alloc_ctx, bytes);
+        return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+      }
+      return cudaMallocAsync(p, bytes, st);
+    };
+    struct Free {
+      const RunSpec &spec;
+      cudaStream_t st;
+      char **slab;
+      Node **nodes;
+      void rel(void *p) {
+        if (!p) return;
+        if (spec.dev_free)
+          spec.dev_free(spec.alloc_ctx, p);
+        else
+          cudaFreeAsync(p, st);
+      }
+      ~Free() {
+        rel(*slab);
+        rel(*nodes);
+      }
+    } free_guard{spec, st, &slab, &nodes};
+    SQ_CU(dalloc((void **)&slab, off));
+    SQ_CU(dalloc((void **)&nodes, sizeof(Node) * node_cap));
+
+    Ctx c;
+    memset(&c, 0, sizeof(c));
+    c.inst = (Inst *)(slab + o_inst);
+    c.nodes = nodes;
+    c.node_cap = (u32)node_cap;
+    for (int cl = 0; cl < kLeafClasses; cl++) c.leaf_cap[cl] = leaf_cap[cl];
+    c.ready_cap = (u32)ready_cap;
+    c.fresh_cap = (u32)fresh_cap;
+    c.status = (Status *)(slab + o_status);
+    c.meta = (u32 *)(slab + o_meta);
+    c.meta_cap = meta_cap;
+    c.done_list = (u32 *)(slab + o_done);
+    c.trace = spec.trace_cap ? (TraceRec *)(slab + o_trace) : nullptr;
+    c.trace_cap = spec.trace_cap;
+    c.cutoff = cutoff;
+    for (int cl = 0; cl < kLeafClasses; cl++) c.class_cap[cl] = class_cap(cl);
+    c.recurse = spec.skew_only ? 0 : 1;
+    Counters *cnt = (Counters *)(slab + o_cnt);
+
+    // ---- seed the roots (host-built records)
+    std::vector<Inst> hinst(ninst);
+    std::vector<Node> hnodes;
+    std::vector<u32> hfresh;
+    std::vector<Leaf> hleaves[kLeafClasses];
+    Counters hc[2];
+    memset(hc, 0, sizeof(hc));
+    Status hs;
+    memset(&hs, 0, sizeof(hs));
+    for (u32 i = 0; i < ninst; i++) {
+      const InstSpec &is = spec.inst[i];
+      hinst[i].keys = is.keys;
+      hinst[i].vals = is.vals;
+      hinst[i].dkeys = is.dkeys;
+      hinst[i].dvals = is.dvals;
+      hinst[i].n = is.n;
+      if (spec.skew_only) continue;
+      if (is.n == 0) {
+        hs.done++;
+        continue;
+      }
+      if (is.n <= cutoff) {
+        int cl = 0;
+        while (cl < NCLASS - 1 && is.n > class_cap(cl)) ++cl;
+        Leaf L;
+        L.off = 0;
+        L.n = (u32)is.n;
+        L.inst = i;
+        L.parent = kNone;
+        L.flags = KIND_ROOT;  // out = A
+        hleaves[cl].push_back(L);
+        hc[0].leaf_elems[cl] += is.n;
+      } else {
+        Node nd;
+        memset(&nd, 0, sizeof(nd));
+        const u32 m = isqrt_ceil(is.n);
+        nd.off = 0;
+        nd.hash = root_hash(is.seed);
+        nd.n = (u32)is.n;
+        nd.rows = nd.cols = nd.k = m;
+        nd.inst = i;
+        nd.parent = kNone;
+        nd.kind = KIND_ROOT;
+        nd.out = 0;
+        hfresh.push_back((u32)hnodes.size());
+        hnodes.push_back(nd);
+      }
+    }
+    if (spec.skew_only) {
+      Node nd;
+      memset(&nd, 0, sizeof(nd));
+      nd.n = (u32)spec.inst[0].n;
+      nd.rows = (u32)spec.rows;
+      nd.cols = (u32)spec.cols;
+      nd.k = (u32)spec.k;
+      nd.parent = kNone;
+      hnodes.push_back(nd);
+      hc[0].ready = 1;
+      hc[0].max_ready_k = nd.k;
+    }
+    for (int cl = 0; cl < NCLASS; cl++) hc[0].leaves[cl] = (u32)hleaves[cl].size();
+    hc[0].fresh = (u32)hfresh.size();
+    hs.nodes_used = (u32)hnodes.size();
+    SQ_CU(cudaMemcpyAsync(c.inst, hinst.data(), sizeof(Inst) * ninst, cudaMemcpyHostToDevice, st));
+    if (!hnodes.empty())
+      SQ_CU(cudaMemcpyAsync(nodes, hnodes.data(), sizeof(Node) * hnodes.size(), cudaMemcpyHostToDevice, st));
+    if (!hfresh.empty())
+      SQ_CU(cudaMemcpyAsync(slab + o_fresh[0], hfresh.data(), 4 * hfresh.size(), cudaMemcpyHostToDevice, st));
+    for (int cl = 0; cl < NCLASS; cl++)
+      if (!hleaves[cl].empty())
+        SQ_CU(cudaMemcpyAsync(slab + o_leaves[0][cl], hleaves[cl].data(), sizeof(Leaf) * hleaves[cl].size(),
+                              cudaMemcpyHostToDevice, st));
+    if (spec.skew_only) {
+      const u32 zero = 0;
+      SQ_CU(cudaMemcpyAsync(slab + o_ready[0], &zero, 4, cudaMemcpyHostToDevice, st));
+    }
+    SQ_CU(cudaMemcpyAsync(cnt, hc, sizeof(hc), cudaMemcpyHostToDevice, st));
+    SQ_CU(cudaMemcpyAsync(c.status, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
+
+    // ---- rounds
+    Launcher L;
+    L.st = st;
+    L.prof = stats_box().profiling.load() != 0;
+    struct Readback {
+      Counters cnt;
+      Status status;
+    };
+    Readback *hrb = nullptr;
+    SQ_CU(cudaMallocHost((void **)&hrb, sizeof(Readback)));
+    struct FreeHost {
+      Readback *p;
+      ~FreeHost() {
+        if (p) cudaFreeHost(p);
+      }
+    } fh{hrb};
+    Counters cur_cnt = hc[0];
+    u32 done = hs.done;
+    int rc = 0;
+    u64 rounds = 0;
+    const int grid_count = nsm * 2, grid_scan = nsm * 8, grid_skew = nsm * 2, grid_expand = nsm * 4;
+    for (u32 r = 0;; r++) {
+      const int cur = r & 1, nxt = cur ^ 1;
+      if (!spec.skew_only && done >= ninst) break;
+      if (spec.skew_only && r == 1) break;
+      if (r > 100000) {
+        snprintf(err, errlen, "recursion did not finish");
+        rc = 8;
+        break;
+      }
+      rounds++;
+      for (int cl = 0; cl < kLeafClasses; cl++) {
+        c.leaves_cur[cl] = (Leaf *)(slab + o_leaves[cur][cl]);
+        c.leaves_nxt[cl] = (Leaf *)(slab + o_leaves[nxt][cl]);
+      }
+      c.ready_cur = (u32 *)(slab + o_ready[cur]);
+      c.ready_nxt = (u32 *)(slab + o_ready[nxt]);
+      c.fresh_cur = (u32 *)(slab + o_fresh[cur]);
+      c.fresh_nxt = (u32 *)(slab + o_fresh[nxt]);
+      c.cnt_cur = cnt + cur;
+      c.cnt_nxt = cnt + nxt;
+      SQ_CU(cudaMemsetAsync(cnt + nxt, 0, sizeof(Counters), st));
+      SQ_CU(cudaMemsetAsync(&c.status->cur_count, 0, 4 * sizeof(u32), st));
+      // leaves (simple_sort)
+      for (int cl = 0; cl < NCLASS; cl++) {
+        if (!cur_cnt.leaves[cl]) continue;
+        L.local.bytes[KF_LEAF] += 2.0 * (KEY_BYTES + 4) * (double)cur_cnt.leaf_elems[cl];
+        SQ_CU(launch_leaf_class(L, c, cl, cur_cnt.leaves[cl]));
+      }
+      // nodes whose columns are sorted: pivots, counts, SkewTranspose, buckets
+      const u32 ready = cur_cnt.ready;
+      if (ready) {
+        const double re = spec.skew_only ? (double)spec.inst[0].n : (double)cur_cnt.ready_elems;
+        L.local.nodes += spec.skew_only ? 0 : ready;
+        L.begin(KF_PLAN);
+        k_plan<<<1, 1024, 0, st>>>(c, ready, K::key_words);
+        L.end();
+        SQ_CU(cudaGetLastError());
+        if (spec.skew_only) {
+          L.begin(KF_AUX);
+          k_put_pivots<DT><<<((u32)spec.k + 255) / 256, 256, 0, st>>>(
+              c, (const typename K::key_t *)spec.piv_keys, spec.piv_vals);
+          L.end();
+          SQ_CU(cudaGetLastError());
+        } else {
+          SQ_CU(launch_all_pivots(L, c, ready, cur_cnt.max_ready_k));
+        }
+        const u32 kmax = std::max<u32>(cur_cnt.max_ready_k, 2);
+        const size_t smem_count = (size_t)(kmax - 1) * sizeof(E) + (size_t)kmax * 4 + 1024 * 4;
+        SQ_CU(set_smem(k_count<DT>, smem_count));
+        L.begin(KF_COUNT);
+        k_count<DT><<<grid_count, 1024, smem_count, st>>>(c, ready, kmax);
+        L.end();
+        L.local.bytes[KF_COUNT] += (KEY_BYTES + 4) * re;
+        SQ_CU(cudaGetLastError());
+        L.begin(KF_SCAN);
+        k_scan<<<grid_scan, 256, 0, st>>>(c, ready, K::key_words);
+        L.end();
+        SQ_CU(cudaGetLastError());
+        L.begin(KF_BSTART);
+        k_bstart<<<ready, 1024, 0, st>>>(c, ready, K::key_words);
+        L.end();
+        SQ_CU(cudaGetLastError());
+        const size_t smem_skew = sizeof(SkewSmem<DT, SKEW_CAP>);
+        SQ_CU(set_smem(k_skew<DT, SKEW_CAP>, smem_skew));
+        L.begin(KF_SKEW);
+        k_skew<DT, SKEW_CAP><<<grid_skew, 256, smem_skew, st>>>(c, ready);
+        L.end();
+        L.local.bytes[KF_SKEW] += 2.0 * (KEY_BYTES + 4) * re;
+        SQ_CU(cudaGetLastError());
+        if (spec.skew_only) {
+          L.begin(KF_AUX);
+          k_get_bstart<DT><<<((u32)spec.k + 256) / 256, 256, 0, st>>>(c, (u64 *)spec.bucket_start);
+          L.end();
+          SQ_CU(cudaGetLastError());
+        } else {
+          L.begin(KF_EXPAND);
+          k_expand_buckets<DT><<<ready, 256, 0, st>>>(c, ready);
+          L.end();
+          SQ_CU(cudaGetLastError());
+        }
+      }
+      if (!spec.skew_only && (ready || cur_cnt.fresh)) {
+        L.begin(KF_EXPAND);
+        k_expand_cols<DT><<<grid_expand, 256, 0, st>>>(c);
+        L.end();
+        SQ_CU(cudaGetLastError());
+      }
+      SQ_CU(cudaMemcpyAsync(&hrb->cnt, cnt + nxt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+      SQ_CU(cudaMemcpyAsync(&hrb->status, c.status, sizeof(Status), cudaMemcpyDeviceToHost, st));
+      SQ_CU(cudaStreamSynchronize(st));
+      L.collect();
+      const Status &S = hrb->status;
+      if (S.error & ~ERRB_TRACE) {
+        snprintf(err, errlen, "engine error bits 0x%x (1 pivot attempts, 2 nodes, 4 list, 8 arena, 16 sizes)",
+                 S.error);
+        rc = (S.error & ERRB_ATTEMPTS) ? 7 : ((S.error & ERRB_SIZES) ? 8 : 2);
+        break;
+      }
+      done = S.done;
+      cur_cnt = hrb->cnt;
+      // grow the node pool so that the next round cannot overflow it
+      if ((u64)S.nodes_used + fresh_cap > node_cap && !spec.skew_only) {
+        const u64 ncap = std::max<u64>(2 * node_cap, (u64)S.nodes_used + 2 * fresh_cap);
+        Node *nn = nullptr;
+        SQ_CU(dalloc((void **)&nn, sizeof(Node) * ncap));
+        SQ_CU(cudaMemcpyAsync(nn, nodes, sizeof(Node) * S.nodes_used, cudaMemcpyDeviceToDevice, st));
+        SQ_CU(cudaStreamSynchronize(st));
+        free_guard.rel(nodes);
+        nodes = nn;
+        node_cap = ncap;
+        c.nodes = nodes;
+        c.node_cap = (u32)std::min<u64>(ncap, 0xffffffffull);
+      }
+    }
+    if (rc == 0 && spec.trace && spec.trace_cap) {
+      Status hs2;
+      SQ_CU(cudaMemcpyAsync(&hs2, c.status, sizeof(Status), cudaMemcpyDeviceToHost, st));
+      SQ_CU(cudaStreamSynchronize(st));
+      const u32 nt = std::min(hs2.trace_used, spec.trace_cap);
+      std::vector<TraceRec> tr(nt);
+      if (nt)
+        SQ_CU(cudaMemcpyAsync(tr.data(), c.trace, sizeof(TraceRec) * nt, cudaMemcpyDeviceToHost, st));
+      SQ_CU(cudaStreamSynchronize(st));
+      for (u32 i = 0; i < nt; i++) {
+        spec.trace[i].off = tr[i].off;
+        spec.trace[i].n = tr[i].n;
+        spec.trace[i].m = tr[i].m;
+        spec.trace[i].hash = tr[i].hash;
+        spec.trace[i].depth = tr[i].depth;
+        spec.trace[i].kind = tr[i].kind;
+        spec.trace[i].attempts = tr[i].attempts;
+        spec.trace[i].index = tr[i].index;
+      }
+      if (spec.trace_count) *spec.trace_count = hs2.trace_used;
+    }
+    {
+      std::lock_guard<std::mutex> g(stats_box().mu);
+      EngineStats &G = stats_box().s;
+      for (int f = 0; f < KF_COUNT_FAMILIES; f++) {
+        G.launches[f] += L.local.launches[f];
+        G.ms[f] += L.local.ms[f];
+        G.bytes[f] += L.local.bytes[f];
+      }
+      G.rounds += rounds;
+      G.nodes += L.local.nodes;
+      G.sorts += spec.skew_only ? 0 : ninst;
+    }
+    return rc;
+  }
+};
+
+}  // namespace sq

@@ -1,0 +1,87 @@
+// Host-side interface of the SquareSort engine (one instantiation per key
+// type).  Plain C++: no CUDA device code here.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sq {
+
+// Kernel families, for launch counts, timings and algorithmic bytes.
+enum KernelFamily : int {
+  KF_LEAF = 0,
+  KF_PLAN,
+  KF_PIVOTS,
+  KF_COUNT,
+  KF_SCAN,
+  KF_BSTART,
+  KF_SKEW,
+  KF_EXPAND,
+  KF_AUX,
+  KF_COUNT_FAMILIES
+};
+
+struct EngineStats {
+  uint64_t launches[KF_COUNT_FAMILIES];
+  double ms[KF_COUNT_FAMILIES];     // summed launch durations (profiling on)
+  double bytes[KF_COUNT_FAMILIES];  // algorithmic bytes moved
+  uint64_t rounds;
+  uint64_t nodes;  // recursing SquareSort calls
+  uint64_t sorts;
+};
+
+// One sort instance as the engine sees it: device buffers only.
+struct InstSpec {
+  void *keys;      // A keys (device)
+  uint32_t *vals;  // A vals (device)
+  void *dkeys;     // D keys scratch (device), same length
+  uint32_t *dvals; // D vals scratch (device)
+  uint64_t n;
+  uint64_t seed;
+};
+
+struct TraceOut {
+  uint64_t off, n, m, hash;
+  uint32_t depth, kind, attempts, index;
+};
+
+struct RunSpec {
+  const InstSpec *inst;  // host array
+  uint32_t ninst;
+  uint32_t cutoff;      // leaf iff n <= cutoff (2 <= cutoff <= max_leaf)
+  TraceOut *trace;      // host array (optional) receiving per-node records
+  uint32_t trace_cap;
+  uint32_t *trace_count;  // out
+  // stand-alone SkewTranspose (no recursion): instance 0, keys_in = dkeys,
+  // keys_out = keys; pivots (k-1) from the caller; bucket starts out.
+  int skew_only;
+  uint64_t rows, cols, k;
+  const void *piv_keys;       // device
+  const uint32_t *piv_vals;   // device
+  uint64_t *bucket_start;     // device, k+1
+  // Optional device allocator for the engine's own scratch (default:
+  // cudaMallocAsync / cudaFreeAsync on the stream).
+  void *(*dev_alloc)(void *ctx, size_t bytes);
+  void (*dev_free)(void *ctx, void *p);
+  void *alloc_ctx;
+};
+
+// Upper bound of the engine's own scratch bytes for a run (admission control).
+uint64_t engine_scratch_bytes(int dtype, uint64_t total_n, uint32_t ninst, uint32_t cutoff);
+
+// Returns 0 or a status code (sq_status values); writes a message on error.
+int engine_run_u32(const RunSpec &spec, cudaStream_t st, char *err, size_t errlen);
+int engine_run_u64(const RunSpec &spec, cudaStream_t st, char *err, size_t errlen);
+int engine_run_f32(const RunSpec &spec, cudaStream_t st, char *err, size_t errlen);
+
+// Sets the calling thread's sq_last_error() message.
+void api_set_error(const char *msg);
+
+// Largest leaf (and pivot sample) the engine sorts in one group, per key type.
+uint32_t engine_max_leaf(int dtype);
+
+// Global statistics (all engines, all threads), and kernel timing switch.
+void engine_stats_get(EngineStats *out);
+void engine_stats_reset();
+void engine_set_profiling(int on);
+
+}  // namespace sq

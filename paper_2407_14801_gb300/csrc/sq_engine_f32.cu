@@ -1,0 +1,14 @@
+// f32 engine instantiation.
+#include "sq_engine.cuh"
+
+namespace sq {
+
+uint64_t engine_scratch_bytes_f32(uint64_t total_n, uint32_t ninst, uint32_t cutoff) {
+  return Engine<DT_F32>::scratch_bytes(total_n, ninst, cutoff);
+}
+
+int engine_run_f32(const RunSpec &spec, cudaStream_t st, char *err, size_t errlen) {
+  return Engine<DT_F32>::run(spec, st, err, errlen);
+}
+
+}  // namespace sq

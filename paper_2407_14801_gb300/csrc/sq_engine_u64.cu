@@ -1,0 +1,14 @@
+// u64 engine instantiation.
+#include "sq_engine.cuh"
+
+namespace sq {
+
+uint64_t engine_scratch_bytes_u64(uint64_t total_n, uint32_t ninst, uint32_t cutoff) {
+  return Engine<DT_U64>::scratch_bytes(total_n, ninst, cutoff);
+}
+
+int engine_run_u64(const RunSpec &spec, cudaStream_t st, char *err, size_t errlen) {
+  return Engine<DT_U64>::run(spec, st, err, errlen);
+}
+
+}  // namespace sq

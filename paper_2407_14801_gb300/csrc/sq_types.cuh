@@ -1,0 +1,275 @@
+// Element order, random source and shared data structures of the SquareSort
+// engine (device and host).  Nothing here is shared with the CPU oracle.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sq {
+
+typedef unsigned long long u64;
+typedef uint32_t u32;
+
+enum : int { DT_U32 = 0, DT_U64 = 1, DT_F32 = 2 };
+
+// Status bits latched by kernels in Status::error.
+enum : u32 {
+  ERRB_ATTEMPTS = 1u,  // pivot sampling exhausted kMaxAttempts
+  ERRB_NODES = 2u,     // node pool full
+  ERRB_LIST = 4u,      // a work list full
+  ERRB_ARENA = 8u,     // per-round metadata arena full
+  ERRB_SIZES = 16u,    // bucket sizes do not add up (internal error)
+  ERRB_TRACE = 32u,    // trace buffer full (records dropped)
+};
+
+constexpr u32 kNone = 0xffffffffu;
+constexpr int kMaxAttempts = 256;  // pivot samples per node before giving up
+constexpr int kLeafClasses = 5;
+
+// Child kinds (Algorithm 1): the root, a column sort, a bucket sort.
+enum : u32 { KIND_ROOT = 0, KIND_COL = 1, KIND_BUC = 2 };
+
+// ------------------------------------------------------------ key order ----
+// Elements are (key, val) pairs ordered by (ordinal(key), val).  ordinal is
+// the identity for uint32/uint64; for float32 bit patterns it is IEEE order
+// with -0 < +0 and every NaN above +inf, all NaNs equal.
+
+__host__ __device__ __forceinline__ u32 f32_ordinal(u32 b) {
+  if ((b & 0x7fffffffu) > 0x7f800000u) return 0xffffffffu;
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// Three-word element: 64-bit compare word plus a 32-bit word.
+struct __align__(16) E3 {
+  u64 k;
+  u32 x;
+  u32 pad;
+};
+
+template <int DT>
+struct KT;
+
+// uint32 keys: one 64-bit word (key << 32 | val), compared as an integer.
+template <>
+struct KT<DT_U32> {
+  typedef u32 key_t;
+  typedef u64 elem_t;
+  static constexpr int key_words = 1;
+  __device__ __forceinline__ static elem_t make(key_t k, u32 v) { return ((u64)k << 32) | v; }
+  __device__ __forceinline__ static key_t key(elem_t e) { return (u32)(e >> 32); }
+  __device__ __forceinline__ static u32 val(elem_t e) { return (u32)e; }
+  __device__ __forceinline__ static bool lt(elem_t a, elem_t b) { return a < b; }
+  __device__ __forceinline__ static bool eq(elem_t a, elem_t b) { return a == b; }
+  __device__ __forceinline__ static elem_t top() { return ~0ull; }
+};
+
+// float32 keys: compare word (ordinal << 32 | val); the raw bits ride along.
+template <>
+struct KT<DT_F32> {
+  typedef u32 key_t;
+  typedef E3 elem_t;
+  static constexpr int key_words = 1;
+  __device__ __forceinline__ static elem_t make(key_t k, u32 v) {
+    E3 e;
+    e.k = ((u64)f32_ordinal(k) << 32) | v;
+    e.x = k;
+    e.pad = 0;
+    return e;
+  }
+  __device__ __forceinline__ static key_t key(elem_t e) { return e.x; }
+  __device__ __forceinline__ static u32 val(elem_t e) { return (u32)e.k; }
+  __device__ __forceinline__ static bool lt(elem_t a, elem_t b) { return a.k < b.k; }
+  __device__ __forceinline__ static bool eq(elem_t a, elem_t b) { return a.k == b.k; }
+  __device__ __forceinline__ static elem_t top() {
+    E3 e;
+    e.k = ~0ull;
+    e.x = 0xffffffffu;
+    e.pad = 0;
+    return e;
+  }
+};
+
+// uint64 keys: (key, val) compared lexicographically.
+template <>
+struct KT<DT_U64> {
+  typedef u64 key_t;
+  typedef E3 elem_t;
+  static constexpr int key_words = 2;
+  __device__ __forceinline__ static elem_t make(key_t k, u32 v) {
+    E3 e;
+    e.k = k;
+    e.x = v;
+    e.pad = 0;
+    return e;
+  }
+  __device__ __forceinline__ static key_t key(elem_t e) { return e.k; }
+  __device__ __forceinline__ static u32 val(elem_t e) { return e.x; }
+  __device__ __forceinline__ static bool lt(elem_t a, elem_t b) {
+    return a.k < b.k || (a.k == b.k && a.x < b.x);
+  }
+  __device__ __forceinline__ static bool eq(elem_t a, elem_t b) { return a.k == b.k && a.x == b.x; }
+  __device__ __forceinline__ static elem_t top() {
+    E3 e;
+    e.k = ~0ull;
+    e.x = 0xffffffffu;
+    e.pad = 0;
+    return e;
+  }
+};
+
+// --------------------------------------------------------- random source ----
+// Counter-based SplitMix64 (Steele, Lea & Flood 2014): every node's pivots
+// are a pure function of (seed, path from the root, attempt).
+//   root hash      F(seed)
+//   column child i F(h + gamma*(2i+1)),  bucket child j F(h + gamma*(2j+2))
+//   attempt a      s_a = F(h ^ (0xd1b54a32d192ed03 * (a+1)))
+//   draw r         F(s_a + gamma*(r+1)); position floor(draw * n / 2^64)
+
+constexpr u64 kGamma = 0x9e3779b97f4a7c15ull;
+
+__host__ __device__ __forceinline__ u64 mix64(u64 z) {
+  z ^= z >> 30;
+  z *= 0xbf58476d1ce4e5b9ull;
+  z ^= z >> 27;
+  z *= 0x94d049bb133111ebull;
+  z ^= z >> 31;
+  return z;
+}
+__host__ __device__ __forceinline__ u64 root_hash(u64 seed) { return mix64(seed); }
+__host__ __device__ __forceinline__ u64 col_hash(u64 h, u64 i) { return mix64(h + kGamma * (2 * i + 1)); }
+__host__ __device__ __forceinline__ u64 buc_hash(u64 h, u64 j) { return mix64(h + kGamma * (2 * j + 2)); }
+__host__ __device__ __forceinline__ u64 attempt_seed(u64 h, u64 a) {
+  return mix64(h ^ (0xd1b54a32d192ed03ull * (a + 1)));
+}
+__host__ __device__ __forceinline__ u64 draw(u64 s, u64 r) { return mix64(s + kGamma * (r + 1)); }
+
+// Smallest m with m*m >= n (n < 2^53).
+__host__ __device__ __forceinline__ u32 isqrt_ceil(u64 n) {
+  if (n == 0) return 0;
+  u64 m = (u64)sqrt((double)n);
+  while (m * m < n) ++m;
+  while (m > 1 && (m - 1) * (m - 1) >= n) --m;
+  return (u32)m;
+}
+
+// ------------------------------------------------------- work structures ----
+
+// One sort instance: the caller's buffers (A) and the scratch copy (D).
+struct Inst {
+  void *keys;  // A keys
+  u32 *vals;   // A vals
+  void *dkeys; // D keys (scratch)
+  u32 *dvals;  // D vals (scratch)
+  u64 n;
+};
+
+// A SquareSort call with n > cutoff (or a stand-alone SkewTranspose).
+// Geometry: `cols` sorted columns of height `rows` (the last one short or
+// empty) and `k` buckets; for SquareSort nodes rows = cols = k = ceil(sqrt n).
+struct Node {
+  u64 off;   // first element in the instance
+  u64 hash;  // path hash
+  u64 meta;  // word offset of this round's metadata in the arena
+  u32 n, rows, cols, k;
+  u32 inst, parent, kind, index;
+  u32 depth, out;  // out: 0 = result lands in A, 1 = in D
+  int pending;     // column children, later bucket children, still running
+  u32 attempts;
+  u32 unit_base, tile_base, srow_base;  // this round's work numbering
+  u32 ncb, nkb, ncs;                    // count blocks, bucket blocks, skew column blocks
+  u32 pad;
+};
+
+// A leaf: sorted in one group of threads (n <= cutoff).
+struct Leaf {
+  u64 off;
+  u32 n, inst, parent, flags;  // flags: kind | out << 8
+};
+
+// Per-parity list counters (zeroed before the round that fills them).
+struct Counters {
+  u32 leaves[kLeafClasses];
+  u32 ready;
+  u32 fresh;
+  u32 max_ready_k;
+  u64 leaf_elems[kLeafClasses];  // elements in each leaf list (for byte counts)
+  u64 ready_elems;
+};
+
+// Global engine status, read back after every round.
+struct Status {
+  u32 error;
+  u32 done;
+  u32 nodes_used;
+  u32 trace_used;
+  // per-round work totals written by the plan step
+  u32 units, tiles, srows;
+  u64 meta_words;
+  // persistent-kernel work cursors
+  u32 cur_count, cur_scan, cur_skew, cur_expand;
+  u32 pad;
+};
+
+// A trace record, one per recursing node (written when its pivots are chosen).
+struct TraceRec {
+  u64 off, n, m, hash;
+  u32 depth, kind, attempts, index;
+};
+
+// Tile geometry (count blocks, skew tiles).
+constexpr int kCountCols = 16;  // columns per count unit (block-total granularity)
+constexpr int kSkewCols = 64;   // columns per skew tile (multiple of kCountCols)
+constexpr int kSkewBkts = 64;   // buckets per skew tile / P-table granularity
+
+// Everything a kernel needs, passed by value.
+struct Ctx {
+  Inst *inst;
+  Node *nodes;
+  u32 node_cap;
+  // lists, current parity (read) and next parity (write)
+  Leaf *leaves_cur[kLeafClasses];
+  Leaf *leaves_nxt[kLeafClasses];
+  u32 leaf_cap[kLeafClasses];
+  u32 *ready_cur, *ready_nxt;
+  u32 ready_cap;
+  u32 *fresh_cur, *fresh_nxt;
+  u32 fresh_cap;
+  Counters *cnt_cur, *cnt_nxt;
+  Status *status;
+  u32 *meta;  // this round's arena (words)
+  u64 meta_cap;
+  u32 *done_list;  // instance ids in completion order
+  TraceRec *trace;
+  u32 trace_cap;
+  u32 cutoff;
+  u32 class_cap[kLeafClasses];  // max elements per leaf class
+  int recurse;                  // 0 for a stand-alone SkewTranspose
+};
+
+// Metadata layout of a ready node (32-bit words from Node::meta), each
+// section 4-word aligned: pivot keys (k-1, kw words each), pivot vals (k-1),
+// T[j][I] block totals -> exclusive prefixes (k * ncb), P[Jb][i] segment
+// starts (nkb * cols), bucket starts b[0..k] (k+1).
+struct MetaLayout {
+  u64 pk, pv, T, P, b, total;
+};
+
+__host__ __device__ __forceinline__ u64 align4(u64 x) { return (x + 3) & ~3ull; }
+
+__host__ __device__ __forceinline__ MetaLayout meta_layout(u32 k, u32 cols, u32 ncb, u32 nkb, int kw) {
+  MetaLayout L;
+  u64 p = 0;
+  L.pk = p;
+  p += align4((u64)(k - 1) * kw);
+  L.pv = p;
+  p += align4(k - 1);
+  L.T = p;
+  p += align4((u64)k * ncb);
+  L.P = p;
+  p += align4((u64)nkb * cols);
+  L.b = p;
+  p += align4((u64)k + 1);
+  L.total = p;
+  return L;
+}
+
+}  // namespace sq

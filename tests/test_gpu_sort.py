@@ -1,0 +1,164 @@
+"""GPU parity: the CUDA SquareSort against the CPU oracle, element by element,
+through the C ABI (via the ctypes binding).
+
+Sorted output must be bit-exact (keys, payloads); the recursion trace (every
+node's offset, size, m, path hash and pivot-sample count) must equal the
+oracle's, which pins the pivot draws, the column partition and the buckets.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def sq():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_14801_gb300 import build
+
+    build.build()
+    import paper_2407_14801_gb300 as sq
+
+    return sq
+
+
+TORCH_VIEW = {"u32": np.int32, "u64": np.int64, "f32": np.float32}
+
+
+def to_dev(a, dtype):
+    bits = a.view(TORCH_VIEW[dtype]) if dtype != "f32" else a
+    return torch.from_numpy(np.ascontiguousarray(bits).copy()).to("cuda")
+
+
+def from_dev(t, dtype):
+    a = t.cpu().numpy()
+    return a.view({"u32": np.uint32, "u64": np.uint64, "f32": np.float32}[dtype])
+
+
+def gpu_sort(sq, keys, vals, dtype, seed, cutoff, trace=True):
+    dk = to_dev(keys, dtype)
+    dv = to_dev(vals, "u32") if vals is not None else None
+    tr = sq.sort(dk, dv, seed=seed, dtype=dtype, cutoff=cutoff, trace_cap=(1 << 20) if trace else 0)
+    torch.cuda.synchronize()
+    return from_dev(dk, dtype), (from_dev(dv, "u32") if dv is not None else None), tr
+
+
+def trace_key(r):
+    return (r["off"], r["depth"], r["kind"], r["index"])
+
+
+def check_against_oracle(sq, keys, vals, dtype, seed, cutoff):
+    gk, gv, gtr = gpu_sort(sq, keys, vals, dtype, seed, cutoff)
+    ok, ov, otr, _ = oracle.sort(keys, vals, seed=seed, cutoff=cutoff, dtype=dtype, trace_cap=1 << 20)
+    bits = (lambda a: a.view(np.uint32)) if dtype == "f32" else (lambda a: a)
+    assert (bits(gk) == bits(ok)).all(), "keys differ"
+    if vals is not None:
+        assert (gv == ov).all(), "payloads differ"
+    assert sorted(gtr, key=trace_key) == sorted(otr, key=trace_key), "recursion trace differs"
+    return len(otr)
+
+
+SIZES = [1, 2, 3, 4, 16, 17, 63, 64, 65, 100, 511, 512, 513, 1000, 2048, 2049, 5000, 8192, 8193, 16384, 16385,
+         40000, 65536, 200003]
+
+
+@pytest.mark.parametrize("cutoff", [2, 3, 16, 64, 512, 2048, 8192, 16384])
+def test_u32_uniform_all_sizes(sq, cutoff):
+    nodes = 0
+    for n in SIZES:
+        if cutoff <= 3 and n > 40000:
+            continue
+        keys = W.uniform_u32(n, 100 + n)
+        nodes += check_against_oracle(sq, keys, W.iota(n), "u32", seed=n, cutoff=cutoff)
+    assert cutoff >= 16384 or nodes > 0
+
+
+@pytest.mark.parametrize("dist", ["sorted", "reverse", "distinct16"])
+@pytest.mark.parametrize("cutoff", [16, 700, 16384])
+def test_u32_distributions(sq, dist, cutoff):
+    for n in [1000, 65536, 300001]:
+        keys = W.U32_DISTRIBUTIONS[dist](n, 7 + n)
+        check_against_oracle(sq, keys, W.iota(n), "u32", seed=3, cutoff=cutoff)
+
+
+@pytest.mark.parametrize("alphabet", [1, 2, 3])
+def test_ties_with_permuted_payload(sq, alphabet):
+    for n, cutoff in [(5000, 16), (70000, 300), (70000, 16384)]:
+        keys = W.small_alphabet_u32(n, alphabet, alphabet)
+        vals = np.random.default_rng(n).permutation(n).astype(np.uint32)
+        check_against_oracle(sq, keys, vals, "u32", seed=alphabet, cutoff=cutoff)
+
+
+def test_config1_workload(sq):
+    """n = 2^16 (a 256 x 256 view), uniform keys from seed 1, index payload."""
+    n = 1 << 16
+    keys = W.uniform_u32(n, 1)
+    for cutoff in (16, 255, 256, 1024, 16384):
+        check_against_oracle(sq, keys, W.iota(n), "u32", seed=1, cutoff=cutoff)
+
+
+@pytest.mark.parametrize("cutoff", [2, 16, 500, 8192])
+def test_u64_zipf(sq, cutoff):
+    for n in [3, 100, 4097, 50000, 150000]:
+        if cutoff == 2 and n > 50000:
+            continue
+        check_against_oracle(sq, W.zipf_u64(n, n), W.iota(n), "u64", seed=5, cutoff=cutoff)
+        check_against_oracle(sq, W.uniform_u64(n, n + 1), W.iota(n), "u64", seed=6, cutoff=cutoff)
+
+
+@pytest.mark.parametrize("cutoff", [2, 16, 500, 8192])
+def test_f32_specials(sq, cutoff):
+    for n in [5, 700, 30000, 150000]:
+        if cutoff == 2 and n > 30000:
+            continue
+        keys = W.normal_f32(n, n, p_inf=0.01, p_negzero=0.01, p_nan=0.01)
+        keys[::37] = np.float32(0.0)
+        check_against_oracle(sq, keys, W.iota(n), "f32", seed=9, cutoff=cutoff)
+    check_against_oracle(sq, np.tile(W.special_f32(), 50), W.iota(21 * 50), "f32", seed=1, cutoff=16)
+
+
+def test_null_payload(sq):
+    n = 100000
+    keys = W.distinct16_u32(n, 4)
+    gk, _, _ = gpu_sort(sq, keys, None, "u32", 2, 1000, trace=False)
+    ok, _, _, _ = oracle.sort(keys, None, seed=2, cutoff=1000)
+    assert (gk == ok).all()
+
+
+def test_host_buffers_are_staged(sq):
+    """sq_sort on host memory (the end-to-end path): copies inside the call."""
+    n = 123457
+    keys = W.uniform_u32(n, 8)
+    vals = W.iota(n)
+    hk, hv = keys.copy(), vals.copy()
+    sq.sort(hk, hv, seed=4, dtype="u32", cutoff=2000)
+    ok, ov, _, _ = oracle.sort(keys, vals, seed=4, cutoff=2000)
+    assert (hk == ok).all() and (hv == ov).all()
+
+
+def test_repeated_pairs_report_attempts_exhausted(sq):
+    """Equal (key, val) pairs make every pivot sample invalid; the bounded
+    redraw loop gives up after 256 samples and the call reports it."""
+    keys = np.full(100, 7, dtype=np.uint32)
+    vals = np.zeros(100, dtype=np.uint32)
+    dk, dv = to_dev(keys, "u32"), to_dev(vals, "u32")
+    with pytest.raises(sq.SquareSortError) as e:
+        sq.sort(dk, dv, seed=1, dtype="u32", cutoff=16)
+    assert e.value.status == 7
+    with pytest.raises(RuntimeError):
+        oracle.sort(keys, vals, seed=1, cutoff=16)
+    # the context is still usable
+    check_against_oracle(sq, W.uniform_u32(1000, 1), W.iota(1000), "u32", seed=1, cutoff=16)
+
+
+def test_empty_and_tiny(sq):
+    for n in (0, 1, 2):
+        keys = W.uniform_u32(n, 3)
+        gk, gv, _ = gpu_sort(sq, keys, W.iota(n), "u32", 1, 2, trace=False)
+        assert (gk == np.sort(keys)).all()
