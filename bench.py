@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 SquareSort.
+
+Default workload (one step = one SquareSort of n = 2^28 uint32 keys with a
+uint32 index payload, a 16384 x 16384 view): the steps cycle through four
+seeded distributions -- uniform over [0, 2^32), that draw ascending, that
+draw descending, and 16 distinct values.  Every step sorts its own copy of
+the input, staged in HBM before the timed region (2 GiB per step, larger
+than L2, so no flush is needed between steps).
+
+Prints one JSON line (rank 0): throughput in Gkeys/s, the dominant kernel's
+HBM roofline, the end-to-end figure through the C ABI with host buffers, the
+CPU oracle's throughput on a bounded sample, and the SM clocks seen.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload plain|batch|serve]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gkeys/s & % HBM roofline, batched/served vs plain SquareSort; serve p50/p99"
+UNIT = "Gkeys/s"
+DISTS = ["uniform", "sorted", "reverse", "distinct16"]
+DIST_SEED = {"uniform": 2, "sorted": 3, "reverse": 4, "distinct16": 5}
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SOURCES = ["sq_kernels.cuh", "sq_sorter.cuh", "sq_types.cuh"]
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2407_14801_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def profiled_traffic(family: str, workload: str):
+    """DRAM bytes per launch of a kernel family from the committed ncu
+    summary, or None when absent or taken on a different kernel source."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    src = kernel_source_hash()
+    with open(p) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) >= 4 and not line.startswith("#") and parts[0] == family and parts[1] == workload:
+                return float(parts[2]) if parts[3] == src else None
+    return None
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx.append(float(p[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- workloads --
+
+def make_inputs_u32(n: int, device):
+    """The four distributions as device tensors (int32 views of uint32)."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+
+    out = {}
+    uni = W.uniform_u32(n, DIST_SEED["uniform"])
+    out["uniform"] = torch.from_numpy(uni.view(np.int32)).to(device)
+    # "sorted" / "reverse" are the seed-3 uniform draw ordered; sorting the
+    # draw on the GPU gives the same bytes as workloads.sorted_u32, faster.
+    draw = torch.from_numpy(W.uniform_u32(n, DIST_SEED["sorted"]).astype(np.int64)).to(device)
+    srt = torch.sort(draw).values
+    out["sorted"] = srt.to(torch.int32)  # values < 2^32 wrap to the int32 view of the uint32 bits
+    draw = torch.from_numpy(W.uniform_u32(n, DIST_SEED["reverse"]).astype(np.int64)).to(device)
+    out["reverse"] = torch.flip(torch.sort(draw).values, [0]).to(torch.int32)
+    del draw, srt
+    out["distinct16"] = torch.from_numpy(W.distinct16_u32(n, DIST_SEED["distinct16"]).view(np.int32)).to(device)
+    return out
+
+
+def check_sorted_u32(keys, vals, orig_keys):
+    """Full-size check on the device: non-decreasing (key, val) order, vals a
+    permutation, every key equal to the original key at its payload index."""
+    import torch
+
+    k = keys.to(torch.int64) & 0xFFFFFFFF
+    v = vals.to(torch.int64) & 0xFFFFFFFF
+    comp = (k - (1 << 31)) * (1 << 32) + v  # order-preserving and inside int64
+    ok = bool((comp[1:] > comp[:-1]).all())
+    n = keys.numel()
+    seen = torch.zeros(n, dtype=torch.bool, device=keys.device)
+    seen[v] = True
+    ok = ok and bool(seen.all())
+    ok = ok and bool((orig_keys[v] == keys).all())
+    return ok
+
+
+# ----------------------------------------------------------- our impl -----
+
+def bench_plain(args, sq, dist, rank, world, local):
+    import numpy as np
+    import torch
+
+    import workloads as W
+
+    dev = torch.device("cuda", local)
+    n = args.n
+    inputs = make_inputs_u32(n, dev)
+    iota = torch.arange(n, dtype=torch.int32, device=dev)
+    total = args.warmup + args.steps
+    seq = [DISTS[i % 4] for i in range(total)]
+    keys = [inputs[d].clone() for d in seq]
+    vals = [iota.clone() for _ in seq]
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    cutoff = args.cutoff
+    for i in range(args.warmup):
+        sq.sort(keys[i], vals[i], seed=i, dtype="u32", cutoff=cutoff)
+    torch.cuda.synchronize()
+    sq.reset_stats()
+    sq.set_profiling(True)
+    vis = [x for x in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if x.strip()]
+    clocks = ClockSampler(int(vis[local]) if local < len(vis) and vis[local].strip().isdigit() else local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dist_mod = dist
+    from paper_2407_14801_gb300 import dist as D
+
+    D.barrier(dist_mod)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    t_wall0 = time.perf_counter()
+    for i in range(args.warmup, total):
+        sq.sort(keys[i], vals[i], seed=i, dtype="u32", cutoff=cutoff)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    D.barrier(dist_mod)
+    clk = clocks.stop()
+    sq.set_profiling(False)
+    st = sq.stats()
+    ms = ev0.elapsed_time(ev1)
+    ms_max = D.max_over_ranks(ms, dist_mod, dev)
+    value = world * args.steps * n / (ms_max / 1e3) / 1e9
+
+    # correctness of every timed step (outside the timed region)
+    ok = all(check_sorted_u32(keys[i], vals[i], inputs[seq[i]]) for i in range(args.warmup, total))
+    del keys, vals
+    torch.cuda.empty_cache()
+
+    # roofline of the dominant kernel family (by summed launch time)
+    fams = [f for f in st["ms"] if st["launches"][f] > 0 and st["bytes"][f] > 0]
+    dom = max(fams, key=lambda f: st["ms"][f])
+    L = st["launches"][dom]
+    bytes_per_launch = st["bytes"][dom] / L
+    avg_ms = st["ms"][dom] / L
+    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    peak, peak_src = measured_peaks()
+    workload_name = f"plain_u32_n{n}"
+    traffic = profiled_traffic(dom, workload_name)
+    roofline = {"bound": "hbm", "kernel": f"k_{dom}", "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_source": f"{peak_src} (copy bandwidth)", "algorithmic_bytes_per_launch": bytes_per_launch,
+                "avg_launch_ms": avg_ms, "launches": L,
+                "family_ms": {f: round(st["ms"][f], 3) for f in st["ms"] if st["launches"][f]}}
+    # whole-step roofline against the ideal one-level traffic 6 w n (w = 8 bytes)
+    step_frac = (6 * 8 * n) / (ms_max / args.steps / 1e3) / 1e9 / peak
+
+    # end to end through the C ABI with host (pinned) buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = bench_e2e(sq, n, min(args.steps, 4), dev, inputs)
+    del inputs
+    torch.cuda.empty_cache()
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": workload_name, "n": n, "view": f"{int(n ** 0.5)}x{int(n ** 0.5)}",
+                   "key": "uint32", "payload": "uint32 original index", "distributions": DISTS,
+                   "distribution_seeds": DIST_SEED, "step_cycle": "step i sorts distribution i mod 4",
+                   "cutoff": sq.get_cutoff("u32") if not cutoff else cutoff,
+                   "l2": "inputs larger than L2 (each step sorts its own 2 GiB copy)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline,
+        "step_hbm_frac_ideal_6wn": round(step_frac, 4),
+        "e2e": e2e,
+        "gpu_launches": int(sum(st["launches"].values())),
+        "rounds_per_step": st["rounds"] / max(1, args.steps),
+        "recursing_nodes_per_step": st["nodes"] / max(1, args.steps),
+        "wall_s": round(t_wall, 4),
+        "clocks": clk,
+        "verified": ok,
+    }
+    return out
+
+
+def bench_e2e(sq, n, steps, dev, inputs):
+    import torch
+
+    hk = torch.empty(n, dtype=torch.int32).pin_memory()
+    hv = torch.empty(n, dtype=torch.int32).pin_memory()
+    iota = torch.arange(n, dtype=torch.int32)
+    src = {d: inputs[d].cpu() for d in DISTS[:steps]}
+    tot = 0.0
+    for i in range(steps):
+        d = DISTS[i % 4]
+        hk.copy_(src[d])
+        hv.copy_(iota)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sq.sort(hk, hv, seed=100 + i, dtype="u32")  # H2D, sort, D2H inside the call
+        tot += time.perf_counter() - t0
+    return {"value": round(steps * n / tot / 1e9, 3), "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+            "d2h_bytes_per_step": 8 * n, "steps": steps, "buffers": "pinned host"}
+
+
+def cpu_baseline(sample_log2: int = 23, budget_s: float = 25.0):
+    """The CPU oracle, single-threaded, on a bounded sample of the workload:
+    the first 2^sample_log2 keys of each distribution's generator."""
+    import numpy as np
+
+    import oracle
+    import workloads as W
+
+    n = 1 << sample_log2
+    done, t = 0, 0.0
+    gens = {"uniform": W.uniform_u32, "sorted": W.sorted_u32, "reverse": W.reverse_u32,
+            "distinct16": W.distinct16_u32}
+    for d in DISTS:
+        k = gens[d](n, DIST_SEED[d])
+        v = W.iota(n)
+        t0 = time.perf_counter()
+        oracle.sort(k, v, seed=1, cutoff=16384)
+        t += time.perf_counter() - t0
+        done += n
+        if t > budget_s:
+            break
+    return {"value": round(done / t / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done // n} x 2^{sample_log2} uint32 keys (first keys of each distribution's generator), "
+                      f"cutoff 16384, single thread", "seconds": round(t, 2)}
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2407_14801_gb300 import dist as D
+
+    rank, world, local = D.rank_world()
+    torch.cuda.set_device(local)
+    dist = D.init()
+    import paper_2407_14801_gb300 as sq
+
+    sq.lib()
+    if args.workload == "plain":
+        out = bench_plain(args, sq, dist, rank, world, local)
+        if rank == 0 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline()
+    elif args.workload == "batch":
+        from paper_2407_14801_gb300 import workload_bench
+
+        out = workload_bench.bench_batch(args, sq, dist, rank, world, local)
+    elif args.workload == "serve":
+        from paper_2407_14801_gb300 import workload_bench
+
+        out = workload_bench.bench_serve(args, sq, dist, rank, world, local)
+    else:
+        raise SystemExit(f"unknown workload {args.workload}")
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------- the reference arm --
+
+def run_reference(args):
+    """The CPU oracle timed on the host cores: each step one bounded sample
+    (2^20 keys) of the workload, cycling through the four distributions."""
+    rank = int(os.environ.get("RANK", 0))
+    if rank != 0:
+        return
+    import oracle
+    import workloads as W
+
+    n = 1 << 20
+    gens = {"uniform": W.uniform_u32, "sorted": W.sorted_u32, "reverse": W.reverse_u32,
+            "distinct16": W.distinct16_u32}
+    samples = [(gens[d](n, DIST_SEED[d]), W.iota(n)) for d in DISTS]
+    for i in range(args.warmup):
+        k, v = samples[i % 4]
+        oracle.sort(k, v, seed=i, cutoff=16384)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        k, v = samples[i % 4]
+        oracle.sort(k, v, seed=i, cutoff=16384)
+    t = time.perf_counter() - t0
+    value = args.steps * n / t / 1e9
+    sample = f"2^20 uint32 keys per step (first keys of each distribution's generator), cutoff 16384"
+    out = {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(t / args.steps * 1e3, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic", "impl": "reference",
+           "config": {"workload": f"plain_u32_n{1 << 28}", "sample_n": n, "distributions": DISTS},
+           "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="plain", choices=["plain", "batch", "serve"])
+    ap.add_argument("--n", type=int, default=1 << 28)
+    ap.add_argument("--cutoff", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("at least 3 warm-up steps are required")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
