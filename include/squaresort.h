@@ -75,7 +75,7 @@ typedef struct {
 } sq_trace_rec;
 
 typedef struct {
-  uint32_t cutoff;        /* leaf iff n <= cutoff; 0 = tuned default; 2..sq_max_leaf(dtype) */
+  uint32_t cutoff;        /* leaf iff n <= cutoff; 0 = the default; 2..sq_max_leaf(dtype) */
   uint32_t trace_cap;     /* capacity of `trace` in records (0 = no trace) */
   sq_trace_rec *trace;    /* host array receiving node records (any order) */
   uint32_t *trace_count;  /* out: records produced (may exceed trace_cap) */
@@ -104,7 +104,7 @@ typedef struct {
   uint32_t *vals_out;
   const void *pivot_keys;
   const uint32_t *pivot_vals;
-  uint64_t k;                  /* buckets; 1 <= k <= sq_max_leaf(dtype) + 1 */
+  uint64_t k;                  /* buckets; 1 <= k <= sqrt(sq_max_n(dtype)) */
   uint64_t *bucket_start_out;  /* k+1 entries */
 } sq_skew_buf;
 
@@ -163,10 +163,12 @@ sq_status sq_serve_destroy(sq_server *srv);
 /* Message of the calling thread's last failing call ("" if none). */
 const char *sq_last_error(void);
 
-/* Largest n accepted by sq_sort for `dtype` ((max leaf + 1)^2). */
+/* Largest n accepted by sq_sort for `dtype`: (p + 1)^2, p the largest
+ * pivot sample one CTA sorts (16384 for SQ_U32, 8192 otherwise). */
 uint64_t sq_max_n(sq_dtype dtype);
 
-/* Largest leaf (and pivot sample) sorted by one thread group. */
+/* Largest leaf sorted directly (the largest allowed cutoff): 65536, by a
+ * cluster of CTAs merging through distributed shared memory. */
 uint32_t sq_max_leaf(sq_dtype dtype);
 
 /* Default leaf cutoff for `dtype` (0 restores the built-in default). */

@@ -132,7 +132,8 @@ const char *sq_last_error(void) { return g_err; }
 uint32_t sq_max_leaf(sq_dtype dtype) { return dtype_ok(dtype) ? sq::engine_max_leaf(dtype) : 0; }
 
 uint64_t sq_max_n(sq_dtype dtype) {
-  const uint64_t m = sq_max_leaf(dtype);
+  if (!dtype_ok(dtype)) return 0;
+  const uint64_t m = sq::engine_max_pivots(dtype);
   return (m + 1) * (m + 1);
 }
 
@@ -206,9 +207,9 @@ sq_status sq_skew_transpose(const sq_skew_buf *buf, uint64_t rows, uint64_t cols
       cols >= (1ull << 32))
     return fail(SQ_ERR_INVALID, "bad shape: n=%llu rows=%llu cols=%llu", (unsigned long long)n,
                 (unsigned long long)rows, (unsigned long long)cols);
-  if (k == 0 || k > (uint64_t)sq::engine_max_leaf(buf->dtype) + 1)
+  if (k == 0 || k > (uint64_t)sq::engine_max_pivots(buf->dtype) + 1)
     return fail(SQ_ERR_INVALID, "k = %llu outside [1, %u]", (unsigned long long)k,
-                sq::engine_max_leaf(buf->dtype) + 1);
+                sq::engine_max_pivots(buf->dtype) + 1);
   if (!buf->bucket_start_out || (n && (!buf->keys_in || !buf->vals_in || !buf->keys_out || !buf->vals_out)) ||
       (k > 1 && (!buf->pivot_keys || !buf->pivot_vals)))
     return fail(SQ_ERR_INVALID, "null buffer");

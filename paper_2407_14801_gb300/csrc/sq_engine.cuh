@@ -37,10 +37,12 @@ struct Engine {
   typedef KT<DT> K;
   typedef typename K::elem_t E;
   static constexpr int NCLASS = LeafCfg<DT>::nclass;
-  static constexpr int SKEW_CAP = sizeof(E) == 8 ? 4096 : 2048;
+  static constexpr int SKEW_CAP = sizeof(E) == 8 ? 2048 : 1024;
   static constexpr size_t KEY_BYTES = sizeof(typename K::key_t);
+  static constexpr u32 kHostExpandCols = 2048;  // roots with this many columns are expanded on the host
 
   static u32 max_leaf() { return class_cap(NCLASS - 1); }
+  static u32 max_pivots() { return LeafCfg<DT>::max_pivots; }
 
   // ---- launch helpers ---------------------------------------------------
   struct Launcher {
@@ -80,9 +82,11 @@ struct Engine {
     }
   };
 
+  // The 48 KiB default covers static plus dynamic shared memory, so any
+  // sizeable dynamic request raises the kernel's limit first.
   template <class Kern>
   static cudaError_t set_smem(Kern kern, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
+    if (bytes <= 32 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   }
 
@@ -100,15 +104,48 @@ struct Engine {
     return cudaGetLastError();
   }
 
+  template <int T, int R, int G>
+  static cudaError_t launch_leaf_cluster(Launcher &L, const Ctx &c, int cls, u32 count) {
+    typedef Sorter<K, T, R, false> S;
+    const size_t smem = (size_t)S::SMEM * sizeof(E);
+    auto kern = k_leaf_cluster<DT, T, R, G>;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(count * G, 1, 1);
+    cfg.blockDim = dim3(T, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = L.st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = G;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    L.begin(KF_LEAF);
+    e = cudaLaunchKernelEx(&cfg, kern, c, cls, count);
+    L.end();
+    return e != cudaSuccess ? e : cudaGetLastError();
+  }
+
   static cudaError_t launch_leaf_class(Launcher &L, const Ctx &c, int cls, u32 count) {
+    constexpr bool wide = sizeof(E) == 8;  // uint32 keys: 1024-thread CTAs fit
     switch (cls) {
       case 0: return launch_leaf<32, 2, true>(L, c, 0, count);
       case 1: return launch_leaf<32, 16, true>(L, c, 1, count);
       case 2: return launch_leaf<128, 16, false>(L, c, 2, count);
       case 3: return launch_leaf<512, 16, false>(L, c, 3, count);
+      case 4:
+        if constexpr (wide) return launch_leaf<1024, 16, false>(L, c, 4, count);
+        else return launch_leaf_cluster<512, 16, 2>(L, c, 4, count);
+      case 5:
+        if constexpr (wide) return launch_leaf_cluster<1024, 16, 2>(L, c, 5, count);
+        else return launch_leaf_cluster<512, 16, 4>(L, c, 5, count);
       default:
-        if constexpr (NCLASS > 4) return launch_leaf<1024, 16, false>(L, c, 4, count);
-        return cudaErrorInvalidValue;
+        if constexpr (wide) return launch_leaf_cluster<1024, 16, 4>(L, c, 6, count);
+        else return launch_leaf_cluster<512, 16, 8>(L, c, 6, count);
     }
   }
 
@@ -132,7 +169,7 @@ struct Engine {
     e = launch_pivots<32, 16, true>(L, c, ready, 0, 512);
     if (e == cudaSuccess && maxp > 512) e = launch_pivots<128, 16, false>(L, c, ready, 512, 2048);
     if (e == cudaSuccess && maxp > 2048) e = launch_pivots<512, 16, false>(L, c, ready, 2048, 8192);
-    if constexpr (NCLASS > 4)
+    if constexpr (LeafCfg<DT>::max_pivots > 8192)
       if (e == cudaSuccess && maxp > 8192) e = launch_pivots<1024, 16, false>(L, c, ready, 8192, 16384);
     return e;
   }
@@ -141,7 +178,8 @@ struct Engine {
   struct Plan {
     u32 leaf_cap[kLeafClasses];
     u64 ready_cap, fresh_cap, node_cap, meta_cap;
-    size_t o_inst, o_leaves[2][kLeafClasses], o_ready[2], o_fresh[2], o_cnt, o_status, o_meta, o_done, o_trace;
+    size_t o_inst, o_leaves[2][kLeafClasses], o_ready[2], o_fresh[2], o_cnt, o_status, o_meta, o_done, o_trace,
+        o_wbase;
     size_t slab_bytes;
   };
 
@@ -192,6 +230,7 @@ struct Engine {
     P.o_meta = carve(4 * P.meta_cap);
     P.o_done = carve(4 * (size_t)std::max<u32>(ninst, 1));
     P.o_trace = carve(sizeof(TraceRec) * (size_t)trace_cap);
+    P.o_wbase = carve(4 * 4 * P.ready_cap);
     P.slab_bytes = off;
     return P;
   }
@@ -219,7 +258,7 @@ struct Engine {
       total_n += spec.inst[i].n;
       max_n = std::max<u64>(max_n, spec.inst[i].n);
     }
-    const u64 lim = (u64)(max_leaf() + 1) * (max_leaf() + 1);
+    const u64 lim = (u64)(max_pivots() + 1) * (max_pivots() + 1);
     if (!spec.skew_only && max_n > lim) {
       snprintf(err, errlen, "n = %llu exceeds the largest supported size %llu for this key type",
                (unsigned long long)max_n, (unsigned long long)lim);
@@ -232,7 +271,7 @@ struct Engine {
     u64 node_cap = P.node_cap;
     const size_t off = P.slab_bytes, o_inst = P.o_inst, o_ready[2] = {P.o_ready[0], P.o_ready[1]};
     const size_t o_fresh[2] = {P.o_fresh[0], P.o_fresh[1]}, o_cnt = P.o_cnt, o_status = P.o_status;
-    const size_t o_meta = P.o_meta, o_done = P.o_done, o_trace = P.o_trace;
+    const size_t o_meta = P.o_meta, o_done = P.o_done, o_trace = P.o_trace, o_wbase = P.o_wbase;
     size_t o_leaves[2][kLeafClasses];
     for (int q = 0; q < 2; q++)
       for (int cl = 0; cl < kLeafClasses; cl++) o_leaves[q][cl] = P.o_leaves[q][cl];
@@ -272,6 +311,7 @@ struct Engine {
     c.node_cap = (u32)node_cap;
     for (int cl = 0; cl < kLeafClasses; cl++) c.leaf_cap[cl] = leaf_cap[cl];
     c.ready_cap = (u32)ready_cap;
+    c.wbase = (u32 *)(slab + o_wbase);
     c.fresh_cap = (u32)fresh_cap;
     c.status = (Status *)(slab + o_status);
     c.meta = (u32 *)(slab + o_meta);
@@ -328,7 +368,27 @@ struct Engine {
         nd.parent = kNone;
         nd.kind = KIND_ROOT;
         nd.out = 0;
-        hfresh.push_back((u32)hnodes.size());
+        const u32 id = (u32)hnodes.size();
+        if (m <= cutoff && m >= kHostExpandCols) {
+          // a large root whose columns are leaves: spawn them here rather than
+          // in one CTA of k_expand_cols
+          const u32 ncol = (u32)((is.n + m - 1) / m);
+          nd.pending = (int)ncol;
+          for (u32 q = 0; q < ncol; q++) {
+            const u64 st0 = (u64)q * m;
+            Leaf L;
+            L.off = st0;
+            L.n = (u32)std::min<u64>(m, is.n - st0);
+            L.inst = i;
+            L.parent = id;
+            L.flags = KIND_COL | (1u << 8);  // columns are sorted from A into D
+            const int cl = class_of(L.n, NCLASS);
+            hleaves[cl].push_back(L);
+            hc[0].leaf_elems[cl] += L.n;
+          }
+        } else {
+          hfresh.push_back(id);
+        }
         hnodes.push_back(nd);
       }
     }
@@ -383,7 +443,7 @@ struct Engine {
     u32 done = hs.done;
     int rc = 0;
     u64 rounds = 0;
-    const int grid_count = nsm * 2, grid_scan = nsm * 8, grid_skew = nsm * 2, grid_expand = nsm * 4;
+    const int grid_count = nsm * 2, grid_scan = nsm * 8, grid_skew = nsm * 4, grid_expand = nsm * 4;
     for (u32 r = 0;; r++) {
       const int cur = r & 1, nxt = cur ^ 1;
       if (!spec.skew_only && done >= ninst) break;
@@ -405,7 +465,7 @@ struct Engine {
       c.cnt_cur = cnt + cur;
       c.cnt_nxt = cnt + nxt;
       SQ_CU(cudaMemsetAsync(cnt + nxt, 0, sizeof(Counters), st));
-      SQ_CU(cudaMemsetAsync(&c.status->cur_count, 0, 4 * sizeof(u32), st));
+      SQ_CU(cudaMemsetAsync(&c.status->cur_count, 0, 5 * sizeof(u32), st));
       // leaves (simple_sort)
       for (int cl = 0; cl < NCLASS; cl++) {
         if (!cur_cnt.leaves[cl]) continue;
@@ -431,7 +491,7 @@ struct Engine {
           SQ_CU(launch_all_pivots(L, c, ready, cur_cnt.max_ready_k));
         }
         const u32 kmax = std::max<u32>(cur_cnt.max_ready_k, 2);
-        const size_t smem_count = (size_t)(kmax - 1) * sizeof(E) + (size_t)kmax * 4 + 1024 * 4;
+        const size_t smem_count = (size_t)(kmax - 1) * sizeof(E) + (size_t)kmax * 4;
         SQ_CU(set_smem(k_count<DT>, smem_count));
         L.begin(KF_COUNT);
         k_count<DT><<<grid_count, 1024, smem_count, st>>>(c, ready, kmax);
@@ -460,7 +520,7 @@ struct Engine {
           SQ_CU(cudaGetLastError());
         } else {
           L.begin(KF_EXPAND);
-          k_expand_buckets<DT><<<ready, 256, 0, st>>>(c, ready);
+          k_expand_buckets<DT><<<grid_expand, 256, 0, st>>>(c, ready);
           L.end();
           SQ_CU(cudaGetLastError());
         }

@@ -79,6 +79,9 @@ void api_set_error(const char *msg);
 // Largest leaf (and pivot sample) the engine sorts in one group, per key type.
 uint32_t engine_max_leaf(int dtype);
 
+// Largest pivot sample (k - 1) of one node; bounds n by (max + 1)^2.
+uint32_t engine_max_pivots(int dtype);
+
 // Global statistics (all engines, all threads), and kernel timing switch.
 void engine_stats_get(EngineStats *out);
 void engine_stats_reset();

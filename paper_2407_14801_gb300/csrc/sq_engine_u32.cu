@@ -20,6 +20,11 @@ void engine_stats_reset() {
 
 void engine_set_profiling(int on) { stats_box().profiling.store(on ? 1 : 0); }
 
+uint32_t engine_max_pivots(int dtype) {
+  return dtype == DT_U32 ? Engine<DT_U32>::max_pivots()
+                         : (dtype == DT_U64 ? Engine<DT_U64>::max_pivots() : Engine<DT_F32>::max_pivots());
+}
+
 uint32_t engine_max_leaf(int dtype) {
   return dtype == DT_U32 ? Engine<DT_U32>::max_leaf()
                          : (dtype == DT_U64 ? Engine<DT_U64>::max_leaf() : Engine<DT_F32>::max_leaf());

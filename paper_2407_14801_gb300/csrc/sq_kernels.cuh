@@ -25,22 +25,28 @@ namespace sq {
 
 template <int DT>
 struct LeafCfg;
+// Leaf classes (elements per class): c0 = warp x 2 (64), c1 = warp x 16
+// (512), c2 = 128 x 16 (2048), c3 = 512 x 16 (8192), c4 = 16384, c5 = 32768,
+// c6 = 65536.  c4..c6 are 1024 x 16 per CTA (uint32 keys: one CTA, then
+// clusters of 2 and 4) or 512 x 16 per CTA (three-word elements: clusters of
+// 2, 4 and 8).  Pivot samples use the single-CTA sorters only.
 template <>
 struct LeafCfg<DT_U32> {
-  static constexpr int nclass = 5;
+  static constexpr int nclass = 7;
+  static constexpr u32 max_pivots = 16384;
 };
 template <>
 struct LeafCfg<DT_F32> {
-  static constexpr int nclass = 4;
+  static constexpr int nclass = 7;
+  static constexpr u32 max_pivots = 8192;
 };
 template <>
 struct LeafCfg<DT_U64> {
-  static constexpr int nclass = 4;
+  static constexpr int nclass = 7;
+  static constexpr u32 max_pivots = 8192;
 };
-// Class c sorts up to class_cap(c) elements: c0 = warp x 2, c1 = warp x 16,
-// c2 = 128 x 16, c3 = 512 x 16, c4 = 1024 x 16 (uint32 keys only).
 __host__ __device__ __forceinline__ u32 class_cap(int c) {
-  return c == 0 ? 64u : c == 1 ? 512u : c == 2 ? 2048u : c == 3 ? 8192u : 16384u;
+  return c == 0 ? 64u : c == 1 ? 512u : c == 2 ? 2048u : c == 3 ? 8192u : c == 4 ? 16384u : c == 5 ? 32768u : 65536u;
 }
 
 __host__ __device__ __forceinline__ int class_of(u32 n, int nclass) {
@@ -61,6 +67,26 @@ __device__ __forceinline__ int upper_bound_e(const typename K::elem_t *piv, int 
       lo = mid + 1;
   }
   return lo;
+}
+
+// Bucket (number of pivots <= e) of an element that every lane of the warp
+// holds, given that it is at least lo: the lanes first probe 32 pivots
+// kSpan apart, then the kSpan pivots of the interval found; larger jumps
+// fall back to a binary search.  Replaces a serial search of log2(np) steps.
+template <class K>
+__device__ __forceinline__ int warp_bucket_from(const typename K::elem_t *piv, int lo, int np,
+                                                const typename K::elem_t &e) {
+  constexpr int kSpan = 4;
+  const int lane = threadIdx.x & 31;
+  int idx = lo + (lane + 1) * kSpan - 1;  // probes lo+3, lo+7, ...
+  bool le = idx < np && !K::lt(e, piv[idx]);
+  u32 m = __ballot_sync(0xffffffffu, le);
+  if (m == 0xffffffffu) return upper_bound_e<K>(piv, lo + 32 * kSpan, np, e);
+  const int base = lo + __popc(m) * kSpan;  // all pivots below base are <= e
+  idx = base + (lane < kSpan - 1 ? lane : kSpan - 1);
+  le = lane < kSpan - 1 && idx < np && !K::lt(e, piv[idx]);
+  m = __ballot_sync(0xffffffffu, le);
+  return base + __popc(m);
 }
 
 static __device__ __forceinline__ u32 block_excl_scan_u32(u32 v, u32 *warp_tot, u32 &total) {
@@ -118,21 +144,39 @@ static __device__ __forceinline__ u64 block_excl_scan_u64(u64 v, u64 *warp_tot, 
   return r;
 }
 
-// Ready-list position of the node owning work item u (nodes are numbered in
-// list order, so *_base increases along the list).
-template <int FIELD>
-__device__ __forceinline__ u32 find_owner(const Ctx &c, u32 ready_count, u32 u) {
-  u32 lo = 0, hi = ready_count;  // last index with base <= u
+// Ready-list position of the node owning work item u: the last entry of the
+// non-decreasing array base[0..cnt) that is <= u (base[0] = 0).  Called by a
+// whole warp; each round narrows the range 32-fold.
+__device__ __forceinline__ u32 warp_find(const u32 *base, u32 cnt, u32 u) {
+  const int lane = threadIdx.x & 31;
+  u32 lo = 0, hi = cnt;
   while (hi - lo > 1) {
-    const u32 mid = (lo + hi) >> 1;
-    const Node &nd = c.nodes[c.ready_cur[mid]];
-    const u32 b = FIELD == 0 ? nd.unit_base : (FIELD == 1 ? nd.tile_base : nd.srow_base);
-    if (b <= u)
-      lo = mid;
-    else
-      hi = mid;
+    const u32 step = (hi - lo + 31) / 32;
+    const u32 idx = lo + lane * step;
+    const bool le = idx < hi && base[idx] <= u;
+    const u32 m = __ballot_sync(0xffffffffu, le);
+    const u32 last = 31 - __clz(m);
+    lo = lo + last * step;
+    hi = min(hi, lo + step);
   }
   return lo;
+}
+
+// Grabs the next work item of a persistent kernel (warp 0) and finds its
+// node; returns the item in *u and the ready-list index in *ri (shared).
+__device__ __forceinline__ void grab_item(const Ctx &c, u32 *cursor, u32 total, int which, u32 ready_count,
+                                          u32 *s_u, u32 *s_ri) {
+  if ((threadIdx.x >> 5) == 0) {
+    u32 u = 0;
+    if ((threadIdx.x & 31) == 0) u = atomicAdd(cursor, 1u);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    u32 ri = 0;
+    if (u < total) ri = warp_find(c.wbase + (u64)which * c.ready_cap, ready_count, u);
+    if ((threadIdx.x & 31) == 0) {
+      *s_u = u;
+      *s_ri = ri;
+    }
+  }
 }
 
 // A finished unit of work (leaf or completed node) reports to its parent.
@@ -193,16 +237,51 @@ __global__ void __launch_bounds__(WARP ? 256 : T) k_leaf(Ctx c, int cls, u32 cou
   }
 }
 
+// A leaf of a cluster class: CTA `rank` of the cluster loads, sorts and
+// stores elements [rank*NC, (rank+1)*NC) of the leaf; the cluster merges.
+template <int DT, int T, int R, int G>
+__global__ void __launch_bounds__(T) k_leaf_cluster(Ctx c, int cls, u32 count) {
+  typedef KT<DT> K;
+  typedef ClusterSorter<K, T, R, G> CS;
+  typedef typename CS::S S;
+  typedef typename K::elem_t E;
+  typedef typename K::key_t key_t;
+  namespace cg = cooperative_groups;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  E *s = reinterpret_cast<E *>(smem_raw);
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const u32 li = blockIdx.x / G;
+  if (li >= count) return;  // the whole cluster
+  const int tid = threadIdx.x;
+  const Leaf L = c.leaves_cur[cls][li];
+  const Inst I = c.inst[L.inst];
+  const u64 off = L.off + (u64)rank * CS::NC;
+  const u32 nr = L.n > (u32)rank * CS::NC ? min((u32)CS::NC, L.n - (u32)rank * CS::NC) : 0u;
+  E x[R];
+  S::load(x, s, tid, (const key_t *)I.keys + off, I.vals + off, nr);
+  CS::sort(x, s, tid);
+  const u32 out = L.flags >> 8;
+  key_t *ok = (key_t *)(out ? I.dkeys : I.keys) + off;
+  u32 *ov = (out ? I.dvals : I.vals) + off;
+  S::store(x, s, tid, ok, ov, nr);
+  cl.sync();
+  if (rank == 0 && tid == 0) {
+    __threadfence();
+    child_done(c, L.parent, L.flags & 0xffu, L.inst);
+  }
+}
+
 // ------------------------------------------------------------------ plan ---
 
 static __global__ void __launch_bounds__(1024) k_plan(Ctx c, u32 ready_count, int kw) {
   __shared__ u64 wt[33];
-  __shared__ u64 carry[4];
-  if (threadIdx.x < 4) carry[threadIdx.x] = 0;
+  __shared__ u64 carry[5];
+  if (threadIdx.x < 5) carry[threadIdx.x] = 0;
   __syncthreads();
   for (u32 base = 0; base < ready_count; base += blockDim.x) {
     const u32 i = base + threadIdx.x;
-    u64 v[4] = {0, 0, 0, 0};
+    u64 v[5] = {0, 0, 0, 0, 0};
     Node *nd = nullptr;
     if (i < ready_count) {
       nd = &c.nodes[c.ready_cur[i]];
@@ -216,24 +295,30 @@ static __global__ void __launch_bounds__(1024) k_plan(Ctx c, u32 ready_count, in
       v[1] = (u64)ncs * nkb;
       v[2] = (nd->k + 31) / 32;
       v[3] = meta_layout(nd->k, nd->cols, ncb, nkb, kw).total;
+      v[4] = (nd->k + kExpandChunk - 1) / kExpandChunk;
     }
-    u64 ex[4], tot[4];
+    u64 ex[5], tot[5];
 #pragma unroll
-    for (int q = 0; q < 4; q++) ex[q] = block_excl_scan_u64(v[q], wt, tot[q]);
+    for (int q = 0; q < 5; q++) ex[q] = block_excl_scan_u64(v[q], wt, tot[q]);
     if (nd) {
       nd->unit_base = (u32)(carry[0] + ex[0]);
       nd->tile_base = (u32)(carry[1] + ex[1]);
       nd->srow_base = (u32)(carry[2] + ex[2]);
       nd->meta = carry[3] + ex[3];
+      c.wbase[i] = nd->unit_base;
+      c.wbase[(u64)c.ready_cap + i] = nd->tile_base;
+      c.wbase[2ull * c.ready_cap + i] = nd->srow_base;
+      c.wbase[3ull * c.ready_cap + i] = (u32)(carry[4] + ex[4]);
     }
     __syncthreads();
-    if (threadIdx.x < 4) carry[threadIdx.x] += tot[threadIdx.x];
+    if (threadIdx.x < 5) carry[threadIdx.x] += tot[threadIdx.x];
     __syncthreads();
   }
   if (threadIdx.x == 0) {
     c.status->units = (u32)carry[0];
     c.status->tiles = (u32)carry[1];
     c.status->srows = (u32)carry[2];
+    c.status->echunks = (u32)carry[4];
     c.status->meta_words = carry[3];
     if (carry[3] > c.meta_cap || carry[1] > 0xffffffffull) atomicOr(&c.status->error, ERRB_ARENA);
   }
@@ -358,11 +443,17 @@ __global__ void __launch_bounds__(WARP ? 256 : T) k_pivots(Ctx c, u32 ready_coun
 }
 
 // ----------------------------------------------------------------- count ---
-// One pass over the sorted columns of a block of kCountCols columns: each
-// thread takes a contiguous chunk, finds the bucket of its first element by
-// binary search over the pivots and walks the rest.  Produces the block's
-// per-bucket totals T[I][j] and, per column, the start P[Jb][i] of every
-// kSkewBkts-bucket segment.
+// One pass over the sorted columns of a block of kCountCols columns
+// (Section 2.2: each sorted column is scanned against the sorted pivots).
+// Every warp streams a contiguous part of the block, one element per lane
+// (coalesced, kCountU groups of loads in flight).  Within a column the
+// buckets of 32 consecutive elements lie between the previous group's last
+// bucket and the bucket of the group's last element, so each lane searches
+// only that range.  Produces the block's per-bucket totals T[I][j] and, per
+// column, the start P[Jb][i] of every kSkewBkts-bucket segment.
+
+constexpr int kCountU = 4;
+constexpr u32 kPiece = 256;  // skew: elements per warp work piece
 
 template <int DT>
 __global__ void __launch_bounds__(1024) k_count(Ctx c, u32 ready_count, u32 kmax) {
@@ -372,17 +463,12 @@ __global__ void __launch_bounds__(1024) k_count(Ctx c, u32 ready_count, u32 kmax
   extern __shared__ __align__(16) unsigned char smem_raw[];
   E *piv = reinterpret_cast<E *>(smem_raw);
   u32 *hist = reinterpret_cast<u32 *>(piv + (kmax > 1 ? kmax - 1 : 1));
-  int *lastb = reinterpret_cast<int *>(hist + kmax);
   __shared__ u32 s_u, s_ri;
-  const int tid = threadIdx.x;
-  const int NT = blockDim.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int NT = blockDim.x, NW = NT >> 5;
   u32 cur = kNone;
   for (;;) {
-    if (tid == 0) {
-      const u32 u = atomicAdd(&c.status->cur_count, 1u);
-      s_u = u;
-      if (u < c.status->units) s_ri = find_owner<0>(c, ready_count, u);
-    }
+    grab_item(c, &c.status->cur_count, c.status->units, 0, ready_count, &s_u, &s_ri);
     __syncthreads();
     const u32 u = s_u;
     if (u >= c.status->units) break;
@@ -402,66 +488,86 @@ __global__ void __launch_bounds__(1024) k_count(Ctx c, u32 ready_count, u32 kmax
     const key_t *dk = (const key_t *)I.dkeys + nd.off;
     const u32 *dv = I.dvals + nd.off;
     u32 *P = meta + ML.P;
+    const u32 rows = nd.rows, n = nd.n, cols = nd.cols, nkb = nd.nkb;
     const u32 Iblk = u - nd.unit_base;
     const u32 i0 = Iblk * kCountCols;
-    const u32 i1 = min(nd.cols, i0 + kCountCols);
-    const u32 q0 = (u32)min((u64)i0 * nd.rows, (u64)nd.n);
-    const u32 q1 = (u32)min((u64)i1 * nd.rows, (u64)nd.n);
+    const u32 i1 = min(cols, i0 + kCountCols);
+    const u32 q0 = (u32)min((u64)i0 * rows, (u64)n);
+    const u32 q1 = (u32)min((u64)i1 * rows, (u64)n);
     const u32 S = q1 - q0;
-    const u32 chunk = (S + NT - 1) / NT;
-    const u32 a = q0 + min(S, (u32)tid * chunk);
-    const u32 b = q0 + min(S, (u32)tid * chunk + chunk);
-    int bprev = -1, firstb = -1, runb = -1;
-    u32 run = 0;
-    if (a < b) {
-      u32 i = a / nd.rows;
-      u32 pos = a - i * nd.rows;
-      u32 len = min(nd.rows, nd.n - i * nd.rows);
-      for (u32 p = a; p < b; p++) {
-        const E e = K::make(dk[p], dv[p]);
-        int bk;
-        if (p == a || pos == 0) {
-          bk = upper_bound_e<K>(piv, 0, np, e);
+    const u32 per_warp = (((S + NW - 1) / NW) + 31) & ~31u;
+    const u32 ws = q0 + min(S, warp * per_warp);
+    const u32 we = q0 + min(S, warp * per_warp + per_warp);
+    // lane position (column i, offset pos) of element ws + lane, advanced 32 per group
+    u32 p_l = ws + lane;
+    u32 ci = p_l / rows, pos = p_l - ci * rows;
+    int carry_b = -1;
+    u32 carry_i = kNone;
+    for (u32 gs = ws; gs < we; gs += 32 * kCountU) {
+      E ev[kCountU];
+#pragma unroll
+      for (int g = 0; g < kCountU; g++) {
+        const u32 p = gs + g * 32 + lane;
+        ev[g] = p < we ? K::make(dk[p], dv[p]) : K::top();
+      }
+#pragma unroll
+      for (int g = 0; g < kCountU; g++) {
+        const u32 gb = gs + g * 32;
+        if (gb >= we) break;
+        const u32 p = gb + lane;
+        const bool valid = p < we;
+        const u32 vmask = __ballot_sync(0xffffffffu, valid);
+        const int lastv = 31 - __clz(vmask);
+        const u32 len = (u64)ci * rows < n ? min(rows, n - ci * rows) : 0;
+        const u32 i_first = __shfl_sync(0xffffffffu, ci, 0);
+        const u32 i_last = __shfl_sync(0xffffffffu, ci, lastv);
+        const E e = ev[g];
+        int b;
+        if (i_first == i_last) {  // one column: buckets are monotone across the group
+          const u32 pos0 = __shfl_sync(0xffffffffu, pos, 0);
+          const int lo = (i_first == carry_i) ? carry_b : (pos0 == 0 ? 0 : 0);
+          const E elast = shfl_e(e, lastv);
+          const int hi = warp_bucket_from<K>(piv, lo, np, elast);
+          b = upper_bound_e<K>(piv, lo, hi, e);
         } else {
-          bk = bprev;
-          const int lim = min(np, bk + 8);
-          while (bk < lim && !K::lt(e, piv[bk])) ++bk;
-          if (bk == lim && bk < np && !K::lt(e, piv[bk])) bk = upper_bound_e<K>(piv, bk, np, e);
+          b = upper_bound_e<K>(piv, 0, np, e);
         }
-        if (p == a) firstb = bk;
-        if (bk == runb) {
-          ++run;
-        } else {
-          if (run) atomicAdd(&hist[runb], run);
-          runb = bk;
-          run = 1;
+        // bucket totals: one atomic per run of equal buckets
+        const int prevb = __shfl_up_sync(0xffffffffu, b, 1);
+        const bool start = valid && (lane == 0 || prevb != b);
+        const u32 smask = __ballot_sync(0xffffffffu, start);
+        if (start) {
+          const u32 higher = smask & ~((2u << lane) - 1u);
+          const u32 nxt = higher ? (u32)(__ffs(higher) - 1) : (u32)__popc(vmask);
+          atomicAdd(&hist[b], nxt - lane);
         }
-        if (p != a || pos == 0) {
-          const int pb = pos == 0 ? -1 : bprev;
-          for (int Jb = (pb + kSkewBkts) / kSkewBkts; Jb <= bk / kSkewBkts; ++Jb) P[(u64)Jb * nd.cols + i] = pos;
+        // segment starts P[Jb][i]: the first position whose bucket reaches Jb*kSkewBkts
+        if (valid) {
+          int bp;
+          if (pos == 0) {
+            bp = -1;
+          } else if (lane > 0) {
+            bp = prevb;
+          } else if (carry_i == ci) {
+            bp = carry_b;
+          } else {  // first element of this warp's range, mid-column
+            const E pe = K::make(dk[p - 1], dv[p - 1]);
+            bp = upper_bound_e<K>(piv, 0, np, pe);
+          }
+          for (int Jb = (bp + kSkewBkts) / kSkewBkts; Jb <= b / kSkewBkts; ++Jb) P[(u64)Jb * cols + ci] = pos;
+          if (pos + 1 == len)
+            for (u32 Jb = b / kSkewBkts + 1; Jb < nkb; ++Jb) P[(u64)Jb * cols + ci] = len;
         }
-        if (pos + 1 == len)
-          for (u32 Jb = bk / kSkewBkts + 1; Jb < nd.nkb; ++Jb) P[(u64)Jb * nd.cols + i] = len;
-        bprev = bk;
-        if (++pos == len) {
-          ++i;
-          pos = 0;
-          len = (u64)i * nd.rows < nd.n ? min(nd.rows, nd.n - i * nd.rows) : 0;
+        carry_b = __shfl_sync(0xffffffffu, b, lastv);
+        carry_i = __shfl_sync(0xffffffffu, ci, lastv);
+        pos += 32;
+        while (pos >= rows) {
+          pos -= rows;
+          ++ci;
         }
       }
-      if (run) atomicAdd(&hist[runb], run);
     }
-    lastb[tid] = bprev;
     __syncthreads();
-    if (a < b) {
-      const u32 i = a / nd.rows;
-      const u32 pos = a - i * nd.rows;
-      if (pos != 0) {  // segment starts between the previous thread's last element and ours
-        const int pb = lastb[tid - 1];
-        for (int Jb = (pb + kSkewBkts) / kSkewBkts; Jb <= firstb / kSkewBkts; ++Jb)
-          P[(u64)Jb * nd.cols + i] = pos;
-      }
-    }
     u32 *T = meta + ML.T;
     for (u32 j = tid; j < nd.k; j += NT) T[(u64)Iblk * nd.k + j] = hist[j];
     __syncthreads();
@@ -477,11 +583,7 @@ static __global__ void __launch_bounds__(256) k_scan(Ctx c, u32 ready_count, int
   __shared__ u32 s_u, s_ri;
   const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
   for (;;) {
-    if (threadIdx.x == 0) {
-      const u32 u = atomicAdd(&c.status->cur_scan, 1u);
-      s_u = u;
-      if (u < c.status->srows) s_ri = find_owner<2>(c, ready_count, u);
-    }
+    grab_item(c, &c.status->cur_scan, c.status->srows, 2, ready_count, &s_u, &s_ri);
     __syncthreads();
     const u32 u = s_u;
     if (u >= c.status->srows) break;
@@ -537,28 +639,46 @@ static __global__ void __launch_bounds__(1024) k_bstart(Ctx c, u32 ready_count, 
 }
 
 // ------------------------------------------------------------------ skew ---
-// SkewTranspose D -> A.  A tile is kSkewCols columns x kSkewBkts buckets:
-// per column the segment [P[Jb][i], P[Jb+1][i]) (about kSkewBkts elements,
-// one coalesced read), per bucket one contiguous run of the output (about
-// kSkewCols elements, one coalesced write).  The tile's elements are taken in
-// column-major order (chunks of CAP), their bucket found among the tile's
-// pivots, and placed bucket-major in shared memory: within a bucket they keep
-// column order and, per column, sorted order -- exactly the order in which
-// Algorithm 2 (and Algorithm 3) append them.
+// SkewTranspose D -> A (Algorithms 2/3).  A tile is kSkewCols columns x
+// kSkewBkts buckets: per column the segment [P[Jb][i], P[Jb+1][i]) (about
+// kSkewBkts elements, a coalesced read), per bucket one contiguous run of the
+// output (about kSkewCols elements, a coalesced write).  The tile's elements
+// are taken in column-major order in chunks of CAP, classified by bucket,
+// counted per (column, bucket), placed bucket-major in shared memory --
+// within a bucket in column order and, per column, in sorted order, which is
+// the order in which Algorithms 2 and 3 append them -- and written out.
+// Tiles are numbered bucket-block-major so that neighbouring column blocks,
+// whose runs of a bucket are adjacent in A, are written at about the same
+// time and merge in L2.  Every step is parallel: prefix sums are warp scans.
 
 template <int DT, int CAP>
 struct SkewSmem {
   typedef typename KT<DT>::elem_t E;
-  E piv[kSkewBkts];
   E in_e[CAP];
   E out_e[CAP];
+  E piv[kSkewBkts];
   u32 base[kSkewBkts], running[kSkewBkts], tot[kSkewBkts], ob[kSkewBkts];
-  u32 seg_start[kSkewCols], seg_pre[kSkewCols + 1];
-  uint16_t first[kSkewCols][kSkewBkts];
-  uint16_t cnt[kSkewCols][kSkewBkts];
+  u32 seg_start[kSkewCols], seg_pre[kSkewCols + 1], piece_pre[kSkewCols + 1];
+  // per (column, bucket) of the chunk: first and last chunk position of its
+  // run (runs are contiguous inside a column); padded, the scans read columns
+  u32 first[kSkewCols][kSkewBkts + 1];
+  u32 last[kSkewCols][kSkewBkts + 1];
+  uint16_t off[kSkewCols][kSkewBkts + 2];  // within a bucket: elements of lower columns
   uint8_t in_j[CAP], in_c[CAP], out_j[CAP];
-  u32 s_u, s_ri;
+  u32 s_u, s_ri, s_S;
 };
+
+__device__ __forceinline__ u32 warp_excl_scan(u32 v, u32 &total) {
+  const int lane = threadIdx.x & 31;
+  u32 inc = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const u32 o = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= d) inc += o;
+  }
+  total = __shfl_sync(0xffffffffu, inc, 31);
+  return inc - v;
+}
 
 template <int DT, int CAP>
 __global__ void __launch_bounds__(256) k_skew(Ctx c, u32 ready_count) {
@@ -566,15 +686,12 @@ __global__ void __launch_bounds__(256) k_skew(Ctx c, u32 ready_count) {
   typedef typename K::elem_t E;
   typedef typename K::key_t key_t;
   typedef SkewSmem<DT, CAP> SM;
+  static_assert(kSkewCols == 32 && kSkewBkts == 64, "warp scans assume 32 columns x 64 buckets");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SM &sm = *reinterpret_cast<SM *>(smem_raw);
-  const int tid = threadIdx.x, NT = blockDim.x;
+  const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5, NW = NT >> 5;
   for (;;) {
-    if (tid == 0) {
-      const u32 u = atomicAdd(&c.status->cur_skew, 1u);
-      sm.s_u = u;
-      if (u < c.status->tiles) sm.s_ri = find_owner<1>(c, ready_count, u);
-    }
+    grab_item(c, &c.status->cur_skew, c.status->tiles, 1, ready_count, &sm.s_u, &sm.s_ri);
     __syncthreads();
     const u32 u = sm.s_u;
     if (u >= c.status->tiles) break;
@@ -582,16 +699,38 @@ __global__ void __launch_bounds__(256) k_skew(Ctx c, u32 ready_count) {
     const MetaLayout ML = meta_layout(nd.k, nd.cols, nd.ncb, nd.nkb, K::key_words);
     const u32 *meta = c.meta + nd.meta;
     const u32 tile = u - nd.tile_base;
-    const u32 Is = tile / nd.nkb, Jb = tile - Is * nd.nkb;
+    const u32 Jb = tile / nd.ncs, Is = tile - Jb * nd.ncs;
     const u32 j0 = Jb * kSkewBkts, nk = min((u32)kSkewBkts, nd.k - j0);
     const u32 i0 = Is * kSkewCols, nc = min((u32)kSkewCols, nd.cols - i0);
-    const Inst I = c.inst[nd.inst];
-    const key_t *dk = (const key_t *)I.dkeys + nd.off;
-    const u32 *dv = I.dvals + nd.off;
-    key_t *ak = (key_t *)I.keys + nd.off;
-    u32 *av = I.vals + nd.off;
-    const key_t *pk = reinterpret_cast<const key_t *>(meta + ML.pk);
     const u32 *P = meta + ML.P;
+    // segments of this tile's columns; warp 0 also forms their prefix sums
+    if (warp == 0) {
+      u32 len_seg = 0, st = 0;
+      if ((u32)lane < nc) {
+        const u32 i = i0 + lane;
+        const u64 cs = (u64)i * nd.rows;
+        const u32 len = cs < nd.n ? (u32)min((u64)nd.rows, nd.n - cs) : 0;
+        u32 s0 = 0, s1 = 0;
+        if (len) {
+          s0 = P[(u64)Jb * nd.cols + i];
+          s1 = Jb + 1 < nd.nkb ? P[(u64)(Jb + 1) * nd.cols + i] : len;
+        }
+        st = (u32)cs + s0;
+        len_seg = s1 - s0;
+      }
+      u32 total;
+      const u32 ex = warp_excl_scan(len_seg, total);
+      sm.seg_start[lane] = st;
+      sm.seg_pre[lane] = ex;
+      if (lane == 0) {
+        sm.seg_pre[nc] = total;
+        sm.s_S = total;
+      }
+    }
+    __syncthreads();
+    const u32 S = sm.s_S;
+    if (S == 0) continue;  // empty tile (common for sorted inputs)
+    const key_t *pk = reinterpret_cast<const key_t *>(meta + ML.pk);
     const u32 *G = meta + ML.T;
     const u32 *b = meta + ML.b;
     if (tid + 1 < (int)nk) sm.piv[tid] = K::make(pk[j0 + tid], meta[ML.pv + j0 + tid]);
@@ -599,83 +738,101 @@ __global__ void __launch_bounds__(256) k_skew(Ctx c, u32 ready_count) {
       sm.base[tid] = b[j0 + tid] + G[(u64)(Is * (kSkewCols / kCountCols)) * nd.k + j0 + tid];
       sm.running[tid] = 0;
     }
-    if (tid < (int)nc) {
-      const u32 i = i0 + tid;
-      const u64 cs = (u64)i * nd.rows;
-      const u32 len = cs < nd.n ? (u32)min((u64)nd.rows, nd.n - cs) : 0;
-      u32 s0 = 0, s1 = 0;
-      if (len) {
-        s0 = P[(u64)Jb * nd.cols + i];
-        s1 = Jb + 1 < nd.nkb ? P[(u64)(Jb + 1) * nd.cols + i] : len;
-      }
-      sm.seg_start[tid] = (u32)cs + s0;
-      sm.seg_pre[tid + 1] = s1 - s0;  // lengths; prefix below
-    }
-    __syncthreads();
-    if (tid == 0) {
-      sm.seg_pre[0] = 0;
-      for (u32 q = 1; q <= nc; q++) sm.seg_pre[q] += sm.seg_pre[q - 1];
-    }
-    __syncthreads();
-    const u32 S = sm.seg_pre[nc];
+    const Inst I = c.inst[nd.inst];
+    const key_t *dk = (const key_t *)I.dkeys + nd.off;
+    const u32 *dv = I.dvals + nd.off;
+    key_t *ak = (key_t *)I.keys + nd.off;
+    u32 *av = I.vals + nd.off;
+    const int npiv = (int)nk - 1;
     for (u32 cs = 0; cs < S; cs += CAP) {
       const u32 L = min((u32)CAP, S - cs);
-      for (u32 q = tid; q < nc * kSkewBkts; q += NT) (&sm.cnt[0][0])[q] = 0;
-      for (u32 ql = tid; ql < L; ql += NT) {
-        const u32 q = cs + ql;
-        u32 lo = 0, hi = nc;  // last column with seg_pre <= q
-        while (hi - lo > 1) {
-          const u32 mid = (lo + hi) >> 1;
-          if (sm.seg_pre[mid] <= q)
-            lo = mid;
-          else
-            hi = mid;
+      for (u32 q = tid; q < kSkewCols * (kSkewBkts + 1); q += NT) {
+        (&sm.first[0][0])[q] = 0xffffffffu;
+        (&sm.last[0][0])[q] = 0;
+      }
+      // pieces of at most kPiece elements of each column's part of the chunk
+      if (warp == 0) {
+        u32 np_c = 0;
+        if ((u32)lane < nc) {
+          const u32 a = max(sm.seg_pre[lane], cs), e_ = min(sm.seg_pre[lane + 1], cs + L);
+          np_c = e_ > a ? (e_ - a + kPiece - 1) / kPiece : 0;
         }
-        const u32 p = sm.seg_start[lo] + (q - sm.seg_pre[lo]);
-        const E e = K::make(dk[p], dv[p]);
-        sm.in_e[ql] = e;
-        sm.in_j[ql] = (uint8_t)upper_bound_e<K>(sm.piv, 0, (int)nk - 1, e);
-        sm.in_c[ql] = (uint8_t)lo;
+        u32 t;
+        const u32 ex = warp_excl_scan(np_c, t);
+        sm.piece_pre[lane] = ex;
+        if (lane == 0) sm.piece_pre[kSkewCols] = t;
       }
       __syncthreads();
-      for (u32 ql = tid; ql < L; ql += NT) {
-        const uint8_t jl = sm.in_j[ql], ci = sm.in_c[ql];
-        if (ql == 0 || sm.in_c[ql - 1] != ci || sm.in_j[ql - 1] != jl) sm.first[ci][jl] = (uint16_t)ql;
-      }
-      __syncthreads();
-      for (u32 ql = tid; ql < L; ql += NT) {
-        const uint8_t jl = sm.in_j[ql], ci = sm.in_c[ql];
-        if (ql + 1 == L || sm.in_c[ql + 1] != ci || sm.in_j[ql + 1] != jl)
-          sm.cnt[ci][jl] = (uint16_t)(ql - sm.first[ci][jl] + 1);
-      }
-      __syncthreads();
-      if (tid < (int)nk) {
-        u32 acc = 0;
-        for (u32 ci = 0; ci < nc; ci++) {
-          const u32 t = sm.cnt[ci][tid];
-          sm.cnt[ci][tid] = (uint16_t)acc;
-          acc += t;
+      // 1. one warp per piece, coalesced reads; buckets are monotone inside a
+      //    column, so each group of 32 searches only between the previous
+      //    group's last bucket and its own last.  Run starts and ends (per
+      //    column and bucket) are recorded with shared-memory min / max.
+      const u32 npieces = sm.piece_pre[kSkewCols];
+      for (u32 pc = warp; pc < npieces; pc += NW) {
+        u32 ci = 0;  // column of this piece: last with piece_pre <= pc
+#pragma unroll
+        for (u32 st = 16; st > 0; st >>= 1)
+          if (ci + st < nc && sm.piece_pre[ci + st] <= pc) ci += st;
+        const u32 a = max(sm.seg_pre[ci], cs);
+        const u32 pa = a + (pc - sm.piece_pre[ci]) * kPiece;
+        const u32 pe = min(min(sm.seg_pre[ci + 1], cs + L), pa + kPiece);
+        int carry_b = -1;
+        for (u32 g = pa; g < pe; g += 32) {
+          const u32 q = g + lane;
+          const bool valid = q < pe;
+          const u32 vmask = __ballot_sync(0xffffffffu, valid);
+          const int lastv = 31 - __clz(vmask);
+          E e = K::top();
+          if (valid) {
+            const u32 p = sm.seg_start[ci] + (q - sm.seg_pre[ci]);
+            e = K::make(dk[p], dv[p]);
+          }
+          const int lo = carry_b < 0 ? 0 : carry_b;
+          const E elast = shfl_e(e, lastv);
+          const int hi = warp_bucket_from<K>(sm.piv, lo, npiv, elast);
+          const int jb = valid ? upper_bound_e<K>(sm.piv, lo, hi, e) : hi;
+          const int prevb = __shfl_up_sync(0xffffffffu, jb, 1);
+          const int nextb = __shfl_down_sync(0xffffffffu, jb, 1);
+          if (valid) {
+            const u32 ql = q - cs;
+            sm.in_e[ql] = e;
+            sm.in_j[ql] = (uint8_t)jb;
+            sm.in_c[ql] = (uint8_t)ci;
+            if (lane == 0 ? jb != carry_b : jb != prevb) atomicMin(&sm.first[ci][jb], ql);
+            if (lane == lastv || nextb != jb) atomicMax(&sm.last[ci][jb], ql);
+          }
+          carry_b = __shfl_sync(0xffffffffu, jb, lastv);
         }
-        sm.tot[tid] = acc;
       }
       __syncthreads();
-      if (tid == 0) {
-        u32 acc = 0;
-        for (u32 jl = 0; jl < nk; jl++) {
-          sm.ob[jl] = acc;
-          acc += sm.tot[jl];
-        }
+      // 2. per bucket: exclusive prefix over columns (off) and total (tot)
+      for (u32 j = warp; j < kSkewBkts; j += NW) {
+        const u32 f = sm.first[lane][j], l = sm.last[lane][j];
+        u32 t;
+        const u32 ex = warp_excl_scan(f <= l ? l - f + 1 : 0, t);
+        sm.off[lane][j] = (uint16_t)ex;
+        if (lane == 0) sm.tot[j] = t;
       }
       __syncthreads();
+      if (warp == 0) {
+        const u32 v0 = sm.tot[2 * lane], v1 = sm.tot[2 * lane + 1];
+        u32 t;
+        const u32 ex = warp_excl_scan(v0 + v1, t);
+        sm.ob[2 * lane] = ex;
+        sm.ob[2 * lane + 1] = ex + v0;
+      }
+      __syncthreads();
+      // 3. bucket-major placement in shared memory
       for (u32 ql = tid; ql < L; ql += NT) {
-        const uint8_t jl = sm.in_j[ql], ci = sm.in_c[ql];
-        const u32 slot = sm.ob[jl] + sm.cnt[ci][jl] + (ql - sm.first[ci][jl]);
+        const u32 jl = sm.in_j[ql], ci = sm.in_c[ql];
+        const u32 slot = sm.ob[jl] + sm.off[ci][jl] + (ql - sm.first[ci][jl]);
         sm.out_e[slot] = sm.in_e[ql];
-        sm.out_j[slot] = jl;
+        sm.out_j[slot] = (uint8_t)jl;
       }
       __syncthreads();
+      // 4. coalesced write of every bucket's run
       for (u32 s = tid; s < L; s += NT) {
-        const uint8_t jl = sm.out_j[s];
+        const u32 jl = sm.out_j[s];
         const u32 dest = sm.base[jl] + sm.running[jl] + (s - sm.ob[jl]);
         const E e = sm.out_e[s];
         if (dest < nd.n) {
@@ -686,7 +843,7 @@ __global__ void __launch_bounds__(256) k_skew(Ctx c, u32 ready_count) {
         }
       }
       __syncthreads();
-      if (tid < (int)nk) sm.running[tid] += sm.tot[tid];
+      if (tid < (int)kSkewBkts) sm.running[tid] += sm.tot[tid];
       __syncthreads();
     }
   }
@@ -775,27 +932,34 @@ static __device__ void spawn_batch(const Ctx &c, bool has, const Child &ch, u32 
   __syncthreads();
 }
 
-// Bucket children of every ready node (Algorithm 1's last loop).
+// Bucket children of every ready node (Algorithm 1's last loop), spawned in
+// work items of kExpandChunk buckets.  Every bucket of a SquareSort node is
+// non-empty (bucket j >= 1 holds pivot j, bucket 0 the minimum), so the node
+// waits for exactly k children.
 template <int DT>
 __global__ void __launch_bounds__(256) k_expand_buckets(Ctx c, u32 ready_count) {
-  __shared__ u32 wt[33];
-  const u32 id = c.ready_cur[blockIdx.x];
-  const Node nd = c.nodes[id];
-  const MetaLayout ML = meta_layout(nd.k, nd.cols, nd.ncb, nd.nkb, KT<DT>::key_words);
-  const u32 *b = c.meta + nd.meta + ML.b;
-  u32 nonempty = 0;
-  for (u32 j = threadIdx.x; j < nd.k; j += blockDim.x) nonempty += b[j + 1] > b[j];
-  u32 tot;
-  block_excl_scan_u32(nonempty, wt, tot);
-  if (threadIdx.x == 0) c.nodes[id].pending = (int)tot;
-  __syncthreads();
-  for (u32 base = 0; base < nd.k; base += blockDim.x) {
-    const u32 j = base + threadIdx.x;
+  __shared__ u32 s_u, s_ri;
+  for (;;) {
+    grab_item(c, &c.status->cur_ebkt, c.status->echunks, 3, ready_count, &s_u, &s_ri);
+    __syncthreads();
+    const u32 u = s_u;
+    if (u >= c.status->echunks) break;
+    const u32 id = c.ready_cur[s_ri];
+    const Node nd = c.nodes[id];
+    const MetaLayout ML = meta_layout(nd.k, nd.cols, nd.ncb, nd.nkb, KT<DT>::key_words);
+    const u32 *b = c.meta + nd.meta + ML.b;
+    const u32 chunk = u - c.wbase[3ull * c.ready_cap + s_ri];
+    if (chunk == 0 && threadIdx.x == 0) c.nodes[id].pending = (int)nd.k;
+    const u32 j = chunk * kExpandChunk + threadIdx.x;
     Child ch;
     bool has = false;
-    if (j < nd.k) {
+    if (threadIdx.x < kExpandChunk && j < nd.k) {
       ch.n = b[j + 1] - b[j];
-      has = ch.n > 0;
+      has = true;
+      if (ch.n == 0) {  // cannot happen for a valid pivot sample
+        atomicOr(&c.status->error, ERRB_SIZES);
+        has = false;
+      }
       ch.off = nd.off + b[j];
       ch.hash = buc_hash(nd.hash, j);
       ch.inst = nd.inst;

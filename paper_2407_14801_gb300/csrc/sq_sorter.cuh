@@ -10,6 +10,8 @@
 // R elements so that the blocked (thread-contiguous) stores and loads hit
 // distinct banks.
 #pragma once
+#include <cooperative_groups.h>
+
 #include "sq_types.cuh"
 
 namespace sq {
@@ -80,13 +82,19 @@ struct Sorter {
 
   // Sorts the group's N elements; on return thread tid holds sorted
   // positions [tid*R, tid*R + R).  Ends with a barrier, so s is free.
+  // Merge rounds whose run pairs lie inside one warp's 32*R elements need
+  // only a warp barrier.
   __device__ static void sort(E (&x)[R], E *s, int tid) {
     network(x);
 #pragma unroll 1
     for (int w = R; w < N; w <<= 1) {
+      const bool warp_local = WARP || 2 * w <= 32 * R;
 #pragma unroll
       for (int k = 0; k < R; k++) s[px(tid * R + k)] = x[k];
-      sync();
+      if (warp_local)
+        __syncwarp();
+      else
+        __syncthreads();
       const int p0 = tid * R;
       const int base = p0 & ~(2 * w - 1);
       const int diag = p0 - base;
@@ -106,15 +114,22 @@ struct Sorter {
       for (int k = 0; k < R; k++) {
         const bool tb = (bi < w) && (ai >= w || K::lt(bv, av));
         x[k] = tb ? bv : av;
-        if (tb) {
-          ++bi;
-          bv = bi < w ? s[px(bb + bi)] : K::top();
-        } else {
-          ++ai;
-          av = ai < w ? s[px(base + ai)] : K::top();
+        if (k + 1 < R) {  // advance the consumed run; one unconditional load
+          const int ni = (tb ? bi : ai) + 1;
+          const bool in = ni < w;
+          const int addr = (tb ? bb : base) + (in ? ni : 0);
+          E nv = s[px(addr)];
+          nv = in ? nv : K::top();
+          ai = tb ? ai : ni;
+          bi = tb ? ni : bi;
+          av = tb ? av : nv;
+          bv = tb ? nv : bv;
         }
       }
-      sync();
+      if (warp_local)
+        __syncwarp();
+      else
+        __syncthreads();
     }
   }
 
@@ -148,6 +163,64 @@ struct Sorter {
       }
     }
     sync();
+  }
+};
+
+// A leaf of up to G*T*R elements sorted by a cluster of G CTAs: each CTA
+// sorts its T*R elements with Sorter, then log2(G) merge rounds run across
+// the cluster, every thread reading the two runs it merges from whichever
+// CTAs' shared memory holds them (distributed shared memory).  Outputs go
+// through registers between rounds, as in the in-CTA rounds.
+template <class K, int T, int R, int G>
+struct ClusterSorter {
+  typedef Sorter<K, T, R, false> S;
+  typedef typename K::elem_t E;
+  static constexpr int NC = T * R;  // elements per CTA
+  static constexpr int N = NC * G;
+
+  __device__ static void sort(E (&x)[R], E *s, int tid) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    S::sort(x, s, tid);
+    const int rank = (int)cl.block_rank();
+    auto at = [&](int gi) -> E { return *cl.map_shared_rank(s + S::px(gi % NC), gi / NC); };
+#pragma unroll 1
+    for (int w = NC; w < N; w <<= 1) {
+#pragma unroll
+      for (int k = 0; k < R; k++) s[S::px(tid * R + k)] = x[k];
+      cl.sync();
+      const int p0 = rank * NC + tid * R;
+      const int base = p0 & ~(2 * w - 1);
+      const int diag = p0 - base;
+      const int bb = base + w;
+      int lo = diag > w ? diag - w : 0, hi = diag < w ? diag : w;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (K::lt(at(bb + diag - 1 - mid), at(base + mid)))
+          hi = mid;
+        else
+          lo = mid + 1;
+      }
+      int ai = lo, bi = diag - lo;
+      E av = ai < w ? at(base + ai) : K::top();
+      E bv = bi < w ? at(bb + bi) : K::top();
+#pragma unroll
+      for (int k = 0; k < R; k++) {
+        const bool tb = (bi < w) && (ai >= w || K::lt(bv, av));
+        x[k] = tb ? bv : av;
+        if (k + 1 < R) {
+          const int ni = (tb ? bi : ai) + 1;
+          const bool in = ni < w;
+          E nv = at((tb ? bb : base) + (in ? ni : 0));
+          nv = in ? nv : K::top();
+          ai = tb ? ai : ni;
+          bi = tb ? ni : bi;
+          av = tb ? av : nv;
+          bv = tb ? nv : bv;
+        }
+      }
+      cl.sync();  // every CTA has read its runs before they are overwritten
+    }
   }
 };
 

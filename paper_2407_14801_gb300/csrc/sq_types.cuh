@@ -23,7 +23,7 @@ enum : u32 {
 
 constexpr u32 kNone = 0xffffffffu;
 constexpr int kMaxAttempts = 256;  // pivot samples per node before giving up
-constexpr int kLeafClasses = 5;
+constexpr int kLeafClasses = 7;
 
 // Child kinds (Algorithm 1): the root, a column sort, a bucket sort.
 enum : u32 { KIND_ROOT = 0, KIND_COL = 1, KIND_BUC = 2 };
@@ -202,10 +202,10 @@ struct Status {
   u32 nodes_used;
   u32 trace_used;
   // per-round work totals written by the plan step
-  u32 units, tiles, srows;
+  u32 units, tiles, srows, echunks;
   u64 meta_words;
   // persistent-kernel work cursors
-  u32 cur_count, cur_scan, cur_skew, cur_expand;
+  u32 cur_count, cur_scan, cur_skew, cur_expand, cur_ebkt;
   u32 pad;
 };
 
@@ -217,8 +217,9 @@ struct TraceRec {
 
 // Tile geometry (count blocks, skew tiles).
 constexpr int kCountCols = 16;  // columns per count unit (block-total granularity)
-constexpr int kSkewCols = 64;   // columns per skew tile (multiple of kCountCols)
+constexpr int kSkewCols = 32;   // columns per skew tile (multiple of kCountCols)
 constexpr int kSkewBkts = 64;   // buckets per skew tile / P-table granularity
+constexpr int kExpandChunk = 256;  // bucket children spawned per work item
 
 // Everything a kernel needs, passed by value.
 struct Ctx {
@@ -233,6 +234,7 @@ struct Ctx {
   u32 ready_cap;
   u32 *fresh_cur, *fresh_nxt;
   u32 fresh_cap;
+  u32 *wbase;  // per ready node, in list order: first count unit, tile, scan row, bucket chunk (4 x ready_cap)
   Counters *cnt_cur, *cnt_nxt;
   Status *status;
   u32 *meta;  // this round's arena (words)

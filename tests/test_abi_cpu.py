@@ -42,7 +42,7 @@ def test_library_exports_every_declared_symbol(sq):
 
 
 def test_limits(sq):
-    assert sq.max_leaf("u32") == 16384 and sq.max_leaf("u64") == 8192 and sq.max_leaf("f32") == 8192
+    assert sq.max_leaf("u32") == 65536 and sq.max_leaf("u64") == 65536 and sq.max_leaf("f32") == 65536
     assert sq.max_n("u32") == 16385 ** 2 >= 1 << 28
     assert sq.max_n("u64") == 8193 ** 2 >= 1 << 26
 
@@ -59,7 +59,7 @@ def test_rejects_bad_arguments_without_a_device(sq):
     buf = sq.SkewBuf(0, 20, None, None, None, None, None, None, 4, None)
     assert L.sq_skew_transpose(ctypes.byref(buf), 4, 4, None) == 1  # n > rows*cols
     assert L.sq_sort_batch(None, 3, None) == 1
-    assert L.sq_set_cutoff(0, 1) == 1 and L.sq_set_cutoff(0, 20000) == 1
+    assert L.sq_set_cutoff(0, 1) == 1 and L.sq_set_cutoff(0, 70000) == 1
     assert L.sq_set_cutoff(0, 300) == 0 and L.sq_get_cutoff(0) == 300
-    assert L.sq_set_cutoff(0, 0) == 0 and L.sq_get_cutoff(0) == 16384
+    assert L.sq_set_cutoff(0, 0) == 0 and L.sq_get_cutoff(0) == 65536
     assert L.sq_sort(None, None, 0, 0, 0, None) == 0  # empty sort is a no-op

@@ -65,31 +65,33 @@ def check_against_oracle(sq, keys, vals, dtype, seed, cutoff):
 
 
 SIZES = [1, 2, 3, 4, 16, 17, 63, 64, 65, 100, 511, 512, 513, 1000, 2048, 2049, 5000, 8192, 8193, 16384, 16385,
-         40000, 65536, 200003]
+         32768, 32769, 40000, 65536, 65537, 200003, 1000003]
 
 
-@pytest.mark.parametrize("cutoff", [2, 3, 16, 64, 512, 2048, 8192, 16384])
+@pytest.mark.parametrize("cutoff", [2, 3, 16, 64, 512, 2048, 8192, 16384, 32768, 65536])
 def test_u32_uniform_all_sizes(sq, cutoff):
     nodes = 0
     for n in SIZES:
-        if cutoff <= 3 and n > 40000:
+        if (cutoff <= 3 and n > 40000) or (cutoff <= 64 and n > 200003):
             continue
         keys = W.uniform_u32(n, 100 + n)
         nodes += check_against_oracle(sq, keys, W.iota(n), "u32", seed=n, cutoff=cutoff)
-    assert cutoff >= 16384 or nodes > 0
+    assert nodes > 0
 
 
 @pytest.mark.parametrize("dist", ["sorted", "reverse", "distinct16"])
-@pytest.mark.parametrize("cutoff", [16, 700, 16384])
+@pytest.mark.parametrize("cutoff", [16, 700, 16384, 65536])
 def test_u32_distributions(sq, dist, cutoff):
-    for n in [1000, 65536, 300001]:
+    for n in [1000, 65536, 300001, 2000000]:
+        if cutoff == 16 and n > 300001:
+            continue
         keys = W.U32_DISTRIBUTIONS[dist](n, 7 + n)
         check_against_oracle(sq, keys, W.iota(n), "u32", seed=3, cutoff=cutoff)
 
 
 @pytest.mark.parametrize("alphabet", [1, 2, 3])
 def test_ties_with_permuted_payload(sq, alphabet):
-    for n, cutoff in [(5000, 16), (70000, 300), (70000, 16384)]:
+    for n, cutoff in [(5000, 16), (70000, 300), (70000, 16384), (900000, 65536)]:
         keys = W.small_alphabet_u32(n, alphabet, alphabet)
         vals = np.random.default_rng(n).permutation(n).astype(np.uint32)
         check_against_oracle(sq, keys, vals, "u32", seed=alphabet, cutoff=cutoff)
@@ -99,22 +101,26 @@ def test_config1_workload(sq):
     """n = 2^16 (a 256 x 256 view), uniform keys from seed 1, index payload."""
     n = 1 << 16
     keys = W.uniform_u32(n, 1)
-    for cutoff in (16, 255, 256, 1024, 16384):
+    for cutoff in (16, 255, 256, 1024, 16384, 65536):
         check_against_oracle(sq, keys, W.iota(n), "u32", seed=1, cutoff=cutoff)
 
 
-@pytest.mark.parametrize("cutoff", [2, 16, 500, 8192])
+@pytest.mark.parametrize("cutoff", [2, 16, 500, 8192, 16384, 32768, 65536])
 def test_u64_zipf(sq, cutoff):
-    for n in [3, 100, 4097, 50000, 150000]:
+    for n in [3, 100, 4097, 50000, 150000, 1000000]:
+        if cutoff <= 16 and n > 150000:
+            continue
         if cutoff == 2 and n > 50000:
             continue
         check_against_oracle(sq, W.zipf_u64(n, n), W.iota(n), "u64", seed=5, cutoff=cutoff)
         check_against_oracle(sq, W.uniform_u64(n, n + 1), W.iota(n), "u64", seed=6, cutoff=cutoff)
 
 
-@pytest.mark.parametrize("cutoff", [2, 16, 500, 8192])
+@pytest.mark.parametrize("cutoff", [2, 16, 500, 8192, 16384, 32768, 65536])
 def test_f32_specials(sq, cutoff):
-    for n in [5, 700, 30000, 150000]:
+    for n in [5, 700, 30000, 150000, 1000000]:
+        if cutoff <= 16 and n > 150000:
+            continue
         if cutoff == 2 and n > 30000:
             continue
         keys = W.normal_f32(n, n, p_inf=0.01, p_negzero=0.01, p_nan=0.01)
