@@ -104,11 +104,22 @@ struct Engine {
     return cudaGetLastError();
   }
 
-  template <int T, int R, int G>
+  template <int T, int R>
+  static cudaError_t launch_leaf_radix(Launcher &L, const Ctx &c, int cls, u32 count) {
+    const size_t smem = RadixSorter<K, T, R>::kSmem;
+    auto kern = k_leaf_radix<DT, T, R>;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    L.begin(KF_LEAF);
+    kern<<<count, T, smem, L.st>>>(c, cls, count);
+    L.end();
+    return cudaGetLastError();
+  }
+
+  template <int T, int R, int G, bool RADIX>
   static cudaError_t launch_leaf_cluster(Launcher &L, const Ctx &c, int cls, u32 count) {
-    typedef Sorter<K, T, R, false> S;
-    const size_t smem = (size_t)S::SMEM * sizeof(E);
-    auto kern = k_leaf_cluster<DT, T, R, G>;
+    const size_t smem = RADIX ? RadixSorter<K, T, R>::kSmem : sizeof(E) * (size_t)Sorter<K, T, R, false>::SMEM;
+    auto kern = k_leaf_cluster<DT, T, R, G, RADIX>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg;
@@ -131,21 +142,20 @@ struct Engine {
   }
 
   static cudaError_t launch_leaf_class(Launcher &L, const Ctx &c, int cls, u32 count) {
-    constexpr bool wide = sizeof(E) == 8;  // uint32 keys: 1024-thread CTAs fit
     switch (cls) {
       case 0: return launch_leaf<32, 2, true>(L, c, 0, count);
       case 1: return launch_leaf<32, 16, true>(L, c, 1, count);
       case 2: return launch_leaf<128, 16, false>(L, c, 2, count);
-      case 3: return launch_leaf<512, 16, false>(L, c, 3, count);
+      case 3: return launch_leaf_radix<512, 16>(L, c, 3, count);
       case 4:
-        if constexpr (wide) return launch_leaf<1024, 16, false>(L, c, 4, count);
-        else return launch_leaf_cluster<512, 16, 2>(L, c, 4, count);
+        if constexpr (sizeof(E) == 8) return launch_leaf_radix<512, 32>(L, c, 4, count);
+        else return launch_leaf_cluster<512, 16, 2, true>(L, c, 4, count);
       case 5:
-        if constexpr (wide) return launch_leaf_cluster<1024, 16, 2>(L, c, 5, count);
-        else return launch_leaf_cluster<512, 16, 4>(L, c, 5, count);
+        if constexpr (sizeof(E) == 8) return launch_leaf_cluster<1024, 16, 2, false>(L, c, 5, count);
+        else return launch_leaf_cluster<512, 16, 4, true>(L, c, 5, count);
       default:
-        if constexpr (wide) return launch_leaf_cluster<1024, 16, 4>(L, c, 6, count);
-        else return launch_leaf_cluster<512, 16, 8>(L, c, 6, count);
+        if constexpr (sizeof(E) == 8) return launch_leaf_cluster<1024, 16, 4, false>(L, c, 6, count);
+        else return launch_leaf_cluster<512, 16, 8, true>(L, c, 6, count);
     }
   }
 

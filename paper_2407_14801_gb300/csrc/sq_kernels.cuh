@@ -27,9 +27,8 @@ template <int DT>
 struct LeafCfg;
 // Leaf classes (elements per class): c0 = warp x 2 (64), c1 = warp x 16
 // (512), c2 = 128 x 16 (2048), c3 = 512 x 16 (8192), c4 = 16384, c5 = 32768,
-// c6 = 65536.  c4..c6 are 1024 x 16 per CTA (uint32 keys: one CTA, then
-// clusters of 2 and 4) or 512 x 16 per CTA (three-word elements: clusters of
-// 2, 4 and 8).  Pivot samples use the single-CTA sorters only.
+// c6 = 65536.  c4..c6 are one CTA of 512 x 32 and clusters of 2 and 4 CTAs
+// of 1024 x 16 (uint32 keys), or clusters of 2, 4 and 8 CTAs of 512 x 16.  Pivot samples use the single-CTA sorters only.
 template <>
 struct LeafCfg<DT_U32> {
   static constexpr int nclass = 7;
@@ -179,6 +178,170 @@ __device__ __forceinline__ void grab_item(const Ctx &c, u32 *cursor, u32 total, 
   }
 }
 
+// ------------------------------------------------------------ radix leaf ---
+// Leaf sort for one CTA: a stable least-significant-digit radix sort of the
+// key ordinals (8-bit digits, one pass per key byte) in shared memory.  Each
+// pass ranks the elements warp by warp (peers with the same digit found by
+// __match_any_sync, in sequence order), forms digit-major / warp-minor
+// offsets with one block scan, and scatters.  A stable key sort equals the
+// (key, val) order exactly when, among equal keys, vals already increase
+// with position -- true at every level of the recursion when vals are the
+// original index; the result is checked and, if the check fails, the CTA
+// sorts the leaf again with the (key, val) merge sort.
+template <class K, int T, int R>
+struct RadixSorter {
+  typedef typename K::key_t key_t;
+  typedef typename K::elem_t E;
+  typedef Sorter<K, T, R, false> MS;
+  static constexpr int W = T / 32;
+  static constexpr int N = T * R;
+  static constexpr int RADIX = 256;
+  static constexpr int PASSES = (int)sizeof(typename K::ord_t);
+  static constexpr int CS = W + 1;  // padded counter row: (digit, warp) at d*CS + w
+  static constexpr size_t kValsOff = sizeof(key_t) * (size_t)N;
+  static constexpr size_t kCntOff = kValsOff + 4 * (size_t)N;
+  static constexpr size_t kScanOff = kCntOff + 4 * (size_t)RADIX * CS;
+  static constexpr size_t kRadixBytes = kScanOff + 4 * 40;
+  static constexpr size_t kMergeBytes = sizeof(E) * (size_t)MS::SMEM;
+  static constexpr size_t kSmem = kRadixBytes > kMergeBytes ? kRadixBytes : kMergeBytes;
+  static_assert(R % 2 == 0 && T % 256 == 0, "ranks are packed in pairs; 8 counters per thread");
+
+  __device__ __forceinline__ static u32 digit(key_t k, int pass) {
+    return (u32)((u64)K::ord_key(k) >> (8 * pass)) & (RADIX - 1);
+  }
+  __device__ __forceinline__ static int striped(int tid, int q) { return (tid >> 5) * (R * 32) + q * 32 + (tid & 31); }
+
+  // Loads n <= N elements into the warp-striped register layout (coalesced).
+  __device__ static void load(key_t (&kx)[R], u32 (&vx)[R], int tid, const key_t *keys, const u32 *vals, u32 n) {
+#pragma unroll
+    for (int q = 0; q < R; q++) {
+      const int p = striped(tid, q);
+      const bool in = (u32)p < n;
+      kx[q] = in ? keys[p] : K::pad_key();
+      vx[q] = in ? vals[p] : 0xffffffffu;
+    }
+  }
+
+  // Sorts; the result is left in shared memory (keys at 0, vals at
+  // kValsOff).  Returns whether [0, n) is in (key, val) order.
+  __device__ static bool sort(key_t (&kx)[R], u32 (&vx)[R], unsigned char *smem, int tid, u32 n) {
+    key_t *sk = reinterpret_cast<key_t *>(smem);
+    u32 *sv = reinterpret_cast<u32 *>(smem + kValsOff);
+    u32 *cnt = reinterpret_cast<u32 *>(smem + kCntOff);
+    u32 *scan = reinterpret_cast<u32 *>(smem + kScanOff);
+    const int lane = tid & 31, w = tid >> 5;
+    const u32 lt = (1u << lane) - 1u;
+#pragma unroll 1
+    for (int pass = 0; pass < PASSES; pass++) {
+      for (int i = tid; i < RADIX * CS; i += T) cnt[i] = 0;
+      __syncthreads();
+      u32 rk[R / 2];
+#pragma unroll
+      for (int q = 0; q < R; q++) {
+        // rank among this warp's elements with the same digit, in sequence
+        // order: the lowest peer reserves the group's slots, all read its base
+        const u32 d = digit(kx[q], pass);
+        const u32 peers = __match_any_sync(0xffffffffu, d);
+        const u32 before = __popc(peers & lt);
+        const int leader = __ffs(peers) - 1;
+        u32 b = 0;
+        if (before == 0) b = atomicAdd(&cnt[d * CS + w], (u32)__popc(peers));
+        b = __shfl_sync(0xffffffffu, b, leader);
+        const u32 r = b + before;
+        if (q & 1)
+          rk[q >> 1] |= r << 16;
+        else
+          rk[q >> 1] = r;
+      }
+      __syncthreads();
+      // exclusive scan of the counters in (digit, warp) order, 8 per thread
+      {
+        const int f0 = tid * 8;
+        u32 loc[8], sum = 0;
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+          const int f = f0 + i, d = f / W, ww = f - d * W;
+          loc[i] = cnt[d * CS + ww];
+          sum += loc[i];
+        }
+        u32 tot;
+        u32 run = block_excl_scan_u32(sum, scan, tot);
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+          const int f = f0 + i, d = f / W, ww = f - d * W;
+          cnt[d * CS + ww] = run;
+          run += loc[i];
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < R; q++) {
+        const u32 d = digit(kx[q], pass);
+        const u32 pos = cnt[d * CS + w] + ((rk[q >> 1] >> ((q & 1) * 16)) & 0xffffu);
+        sk[pos] = kx[q];
+        sv[pos] = vx[q];
+      }
+      __syncthreads();
+      if (pass + 1 < PASSES) {
+#pragma unroll
+        for (int q = 0; q < R; q++) {
+          const int p = striped(tid, q);
+          kx[q] = sk[p];
+          vx[q] = sv[p];
+        }
+      }
+    }
+    // (key, val) order check over [0, n)
+    bool bad = false;
+#pragma unroll 4
+    for (int q = 0; q < R; q++) {
+      const u32 i = (u32)tid * R + q;
+      if (i + 1 < n && K::ord_key(sk[i]) == K::ord_key(sk[i + 1]) && sv[i] > sv[i + 1]) bad = true;
+    }
+    return !__syncthreads_or(bad);
+  }
+
+  // Blocked register copy of the sorted smem contents (for merges).
+  __device__ static void to_blocked(E (&x)[R], unsigned char *smem, int tid) {
+    const key_t *sk = reinterpret_cast<const key_t *>(smem);
+    const u32 *sv = reinterpret_cast<const u32 *>(smem + kValsOff);
+#pragma unroll
+    for (int q = 0; q < R; q++) x[q] = K::make(sk[tid * R + q], sv[tid * R + q]);
+    __syncthreads();
+  }
+
+  // Coalesced store of the first n sorted elements from shared memory.
+  __device__ static void store(unsigned char *smem, int tid, key_t *keys, u32 *vals, u32 n) {
+    const key_t *sk = reinterpret_cast<const key_t *>(smem);
+    const u32 *sv = reinterpret_cast<const u32 *>(smem + kValsOff);
+#pragma unroll
+    for (int q = 0; q < R; q++) {
+      const int p = q * T + tid;
+      if ((u32)p < n) {
+        keys[p] = sk[p];
+        vals[p] = sv[p];
+      }
+    }
+  }
+
+  // The whole leaf: radix sort, check, merge-sort fallback, store.
+  __device__ static void sort_leaf(unsigned char *smem, int tid, const key_t *ik, const u32 *iv, key_t *okk,
+                                   u32 *ov, u32 n) {
+    key_t kx[R];
+    u32 vx[R];
+    load(kx, vx, tid, ik, iv, n);
+    if (sort(kx, vx, smem, tid, n)) {
+      store(smem, tid, okk, ov, n);
+    } else {
+      E x[R];
+      to_blocked(x, smem, tid);
+      E *s = reinterpret_cast<E *>(smem);
+      MS::sort(x, s, tid);
+      MS::store(x, s, tid, okk, ov, n);
+    }
+  }
+};
+
 // A finished unit of work (leaf or completed node) reports to its parent.
 static __device__ void child_done(const Ctx &c, u32 parent, u32 kind, u32 inst) {
   for (;;) {
@@ -237,10 +400,31 @@ __global__ void __launch_bounds__(WARP ? 256 : T) k_leaf(Ctx c, int cls, u32 cou
   }
 }
 
+// A leaf of a one-CTA class, radix-sorted (see RadixSorter).
+template <int DT, int T, int R>
+__global__ void __launch_bounds__(T, (R <= 16 && sizeof(typename KT<DT>::elem_t) == 8) ? 2 : 1) k_leaf_radix(Ctx c, int cls, u32 count) {
+  typedef KT<DT> K;
+  typedef RadixSorter<K, T, R> RS;
+  typedef typename K::key_t key_t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const u32 li = blockIdx.x;
+  if (li >= count) return;
+  const Leaf L = c.leaves_cur[cls][li];
+  const Inst I = c.inst[L.inst];
+  const u32 out = L.flags >> 8;
+  RS::sort_leaf(smem_raw, threadIdx.x, (const key_t *)I.keys + L.off, I.vals + L.off,
+                (key_t *)(out ? I.dkeys : I.keys) + L.off, (out ? I.dvals : I.vals) + L.off, L.n);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    child_done(c, L.parent, L.flags & 0xffu, L.inst);
+  }
+}
+
 // A leaf of a cluster class: CTA `rank` of the cluster loads, sorts and
 // stores elements [rank*NC, (rank+1)*NC) of the leaf; the cluster merges.
-template <int DT, int T, int R, int G>
-__global__ void __launch_bounds__(T) k_leaf_cluster(Ctx c, int cls, u32 count) {
+template <int DT, int T, int R, int G, bool RADIX>
+__global__ void __launch_bounds__(T, 1) k_leaf_cluster(Ctx c, int cls, u32 count) {
   typedef KT<DT> K;
   typedef ClusterSorter<K, T, R, G> CS;
   typedef typename CS::S S;
@@ -258,9 +442,22 @@ __global__ void __launch_bounds__(T) k_leaf_cluster(Ctx c, int cls, u32 count) {
   const Inst I = c.inst[L.inst];
   const u64 off = L.off + (u64)rank * CS::NC;
   const u32 nr = L.n > (u32)rank * CS::NC ? min((u32)CS::NC, L.n - (u32)rank * CS::NC) : 0u;
+  // this CTA's part: radix sort (merge sort if the (key, val) check fails),
+  // then the cross-CTA merge rounds
+  typedef RadixSorter<K, T, R> RS;
   E x[R];
-  S::load(x, s, tid, (const key_t *)I.keys + off, I.vals + off, nr);
-  CS::sort(x, s, tid);
+  if constexpr (RADIX) {
+    key_t kx[R];
+    u32 vx[R];
+    RS::load(kx, vx, tid, (const key_t *)I.keys + off, I.vals + off, nr);
+    const bool ok = RS::sort(kx, vx, smem_raw, tid, nr);
+    RS::to_blocked(x, smem_raw, tid);
+    if (!ok) S::sort(x, s, tid);
+  } else {
+    S::load(x, s, tid, (const key_t *)I.keys + off, I.vals + off, nr);
+    S::sort(x, s, tid);
+  }
+  CS::merge_rounds(x, s, tid);
   const u32 out = L.flags >> 8;
   key_t *ok = (key_t *)(out ? I.dkeys : I.keys) + off;
   u32 *ov = (out ? I.dvals : I.vals) + off;

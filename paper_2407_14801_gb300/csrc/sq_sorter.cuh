@@ -179,9 +179,14 @@ struct ClusterSorter {
   static constexpr int N = NC * G;
 
   __device__ static void sort(E (&x)[R], E *s, int tid) {
+    S::sort(x, s, tid);
+    merge_rounds(x, s, tid);
+  }
+
+  // The cross-CTA rounds only: x holds this CTA's sorted run, blocked.
+  __device__ static void merge_rounds(E (&x)[R], E *s, int tid) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
-    S::sort(x, s, tid);
     const int rank = (int)cl.block_rank();
     auto at = [&](int gi) -> E { return *cl.map_shared_rank(s + S::px(gi % NC), gi / NC); };
 #pragma unroll 1

@@ -53,7 +53,10 @@ template <>
 struct KT<DT_U32> {
   typedef u32 key_t;
   typedef u64 elem_t;
+  typedef u32 ord_t;
   static constexpr int key_words = 1;
+  __device__ __forceinline__ static ord_t ord_key(key_t k) { return k; }
+  __device__ __forceinline__ static key_t pad_key() { return 0xffffffffu; }
   __device__ __forceinline__ static elem_t make(key_t k, u32 v) { return ((u64)k << 32) | v; }
   __device__ __forceinline__ static key_t key(elem_t e) { return (u32)(e >> 32); }
   __device__ __forceinline__ static u32 val(elem_t e) { return (u32)e; }
@@ -67,7 +70,10 @@ template <>
 struct KT<DT_F32> {
   typedef u32 key_t;
   typedef E3 elem_t;
+  typedef u32 ord_t;
   static constexpr int key_words = 1;
+  __device__ __forceinline__ static ord_t ord_key(key_t k) { return f32_ordinal(k); }
+  __device__ __forceinline__ static key_t pad_key() { return 0xffffffffu; }  // a NaN: ordinal max
   __device__ __forceinline__ static elem_t make(key_t k, u32 v) {
     E3 e;
     e.k = ((u64)f32_ordinal(k) << 32) | v;
@@ -93,7 +99,10 @@ template <>
 struct KT<DT_U64> {
   typedef u64 key_t;
   typedef E3 elem_t;
+  typedef u64 ord_t;
   static constexpr int key_words = 2;
+  __device__ __forceinline__ static ord_t ord_key(key_t k) { return k; }
+  __device__ __forceinline__ static key_t pad_key() { return ~0ull; }
   __device__ __forceinline__ static elem_t make(key_t k, u32 v) {
     E3 e;
     e.k = k;
