@@ -160,6 +160,22 @@ def check_sorted_u32(keys, vals, orig_keys):
     return ok
 
 
+def np_sorted_ok(k0, v0, k, v, dt) -> bool:
+    """Host check of one served request: the output is the input ordered by
+    (ordinal(key), val), float32 by IEEE order with NaNs last and tied."""
+    import numpy as np
+
+    if dt == "f32":
+        b = k0.view(np.uint32).astype(np.uint64)
+        nan = (b & 0x7FFFFFFF) > 0x7F800000
+        ords = np.where(nan, 0xFFFFFFFF, np.where(b & 0x80000000, b ^ 0xFFFFFFFF, b | 0x80000000))
+        bits0, bits = k0.view(np.uint32), k.view(np.uint32)
+    else:
+        ords, bits0, bits = k0, k0, k
+    order = np.lexsort((v0, ords))
+    return bool((v == v0[order]).all() and (bits == bits0[order]).all())
+
+
 # ----------------------------------------------------------- our impl -----
 
 def bench_plain(args, sq, dist, rank, world, local):
@@ -323,19 +339,150 @@ def run_ours(args):
         if rank == 0 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline()
     elif args.workload == "batch":
-        from paper_2407_14801_gb300 import workload_bench
-
-        out = workload_bench.bench_batch(args, sq, dist, rank, world, local)
+        out = bench_batch(args, sq, dist, rank, world, local)
     elif args.workload == "serve":
-        from paper_2407_14801_gb300 import workload_bench
-
-        out = workload_bench.bench_serve(args, sq, dist, rank, world, local)
+        out = bench_serve(args, sq, dist, rank, world, local)
     else:
         raise SystemExit(f"unknown workload {args.workload}")
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------- batched and served ----
+
+def bench_batch(args, sq, dist, rank, world, local):
+    """4096 independent uint32 instances, sizes log-uniform in [2^8, 2^20],
+    uniform keys, index payload, seed 7: one sq_sort_batch call per step
+    against one sq_sort call per instance.  Ranks take disjoint shares."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2407_14801_gb300 import dist as D
+
+    dev = torch.device("cuda", local)
+    count = args.batch_count
+    sizes = W.batch_sizes(count, 7)
+    mine = list(D.shard(count, rank, world))
+    src = [torch.from_numpy(W.uniform_u32(int(sizes[i]), (7 << 20) + i + 1).view(np.int32)).to(dev) for i in mine]
+    keys = [t.clone() for t in src]
+    vals = [torch.arange(t.numel(), dtype=torch.int32, device=dev) for t in src]
+    total_keys = int(sum(t.numel() for t in src))
+    stream = torch.cuda.current_stream()
+
+    def restore():
+        for k, s0, v in zip(keys, src, vals):
+            k.copy_(s0)
+            v.copy_(torch.arange(v.numel(), dtype=torch.int32, device=dev))
+        torch.cuda.synchronize()
+
+    def run_batched():
+        sq.sort_batch([(k, v, 7 + i) for i, (k, v) in enumerate(zip(keys, vals))])
+
+    def run_single():
+        for i, (k, v) in enumerate(zip(keys, vals)):
+            sq.sort(k, v, seed=7 + i, dtype="u32")
+
+    def timed(fn, steps, warm):
+        for _ in range(warm):
+            restore()
+            fn()
+        tot = 0.0
+        for _ in range(steps):
+            restore()
+            D.barrier(dist)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        return D.max_over_ranks(tot, dist, dev) / steps
+
+    sq.reset_stats()
+    ms_b = timed(run_batched, args.steps, args.warmup)
+    st = sq.stats()
+    ms_s = timed(run_single, max(1, args.steps // 4), 1)
+    # correctness of the last batched step is checked instance by instance
+    restore()
+    run_batched()
+    ok = all(check_sorted_u32(k, v, s0) for k, v, s0 in zip(keys, vals, src))
+    all_keys = int(sizes.sum())
+    gk_b = world * total_keys / (ms_b / 1e3) / 1e9
+    gk_s = world * total_keys / (ms_s / 1e3) / 1e9
+    return {"metric": METRIC, "value": round(gk_b, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_b, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"batch_u32_{count}_instances_2^8..2^20", "instances": count,
+                       "total_keys": all_keys, "seed": 7, "cutoff": sq.get_cutoff("u32"),
+                       "parallelism": f"instances sharded over {world} rank(s)"},
+            "per_instance_launches": {"value": round(gk_s, 3), "unit": UNIT, "ms_per_step": round(ms_s, 3)},
+            "batched_over_per_instance": round(ms_s / ms_b, 2),
+            "gpu_launches_per_step": sum(st["launches"].values()) / max(1, args.steps + args.warmup),
+            "rounds_per_step": st["rounds"] / max(1, args.steps + args.warmup), "verified": ok}
+
+
+def bench_serve(args, sq, dist, rank, world, local):
+    """A Poisson stream of sort requests (sizes log-uniform in [2^10, 2^24],
+    key type uniform over uint32 / uint64 / float32, index payload) served
+    under a 16 GiB budget at 80% of the saturation rate measured by a
+    closed-loop run; reports keys/s and p50/p99 submit-to-done latency."""
+    import numpy as np
+
+    import workloads as W
+
+    nreq = args.serve_requests
+    reqs = W.serve_requests(nreq, 11, rate_per_s=1.0)  # arrival times rescaled below
+    inputs = [(W.keys_for(dt, n, ks), W.iota(n), dt) for (_, n, dt, ks) in reqs]
+    budget = 16 << 30
+
+    def run(rate):
+        bufs = [(k.copy(), v.copy(), dt) for k, v, dt in inputs]
+        srv = sq.Server(budget, device=local)
+        lat, tickets = [], []
+        t0 = time.perf_counter()
+        arrivals = [a / rate for (a, _, _, _) in reqs] if rate else [0.0] * nreq
+        pending = {}
+        i = 0
+        while i < nreq or pending:
+            now = time.perf_counter() - t0
+            while i < nreq and arrivals[i] <= now:
+                k, v, dt = bufs[i]
+                pending[srv.submit(k, v, seed=i, dtype=dt)] = i
+                i += 1
+            for t in list(pending):
+                r = srv.poll(t)
+                if r is not None:
+                    if r[0] != 0:
+                        raise RuntimeError(f"request {pending[t]} failed with status {r[0]}")
+                    lat.append(r[1])
+                    del pending[t]
+            if i < nreq and not pending:
+                time.sleep(max(0.0, min(arrivals[i] - (time.perf_counter() - t0), 0.001)))
+            else:
+                time.sleep(0.0002)
+        wall = time.perf_counter() - t0
+        srv.close()
+        return wall, lat, bufs
+
+    keys_total = sum(n for (_, n, _, _) in reqs)
+    wall_sat, _, _ = run(0.0)  # closed loop: everything submitted at once
+    sat_rps = nreq / wall_sat
+    wall, lat, bufs = run(0.8 * sat_rps)
+    ok = all(np_sorted_ok(k0, v0, k, v, dt) for (k0, v0, dt), (k, v, _) in zip(inputs[:32], bufs[:32]))
+    lat = np.array(lat)
+    return {"metric": METRIC, "value": round(keys_total / wall / 1e9, 3), "unit": UNIT, "n_gpus": world,
+            "steps": nreq, "warmup": 0, "ms_per_step": round(wall / nreq * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64/f32", "data": "synthetic",
+            "config": {"workload": f"serve_{nreq}_poisson_requests_2^10..2^24", "requests": nreq,
+                       "mean_keys": keys_total / nreq, "budget_bytes": budget,
+                       "arrival_rate_rps": round(0.8 * sat_rps, 2), "saturation_rps": round(sat_rps, 2),
+                       "saturation_keys_per_s": round(keys_total / wall_sat / 1e9, 3)},
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "mean": float(lat.mean())},
+            "verified_sample": ok}
 
 
 # ----------------------------------------------------- the reference arm --
@@ -384,6 +531,8 @@ def main():
     ap.add_argument("--cutoff", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--serve-requests", type=int, default=512)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps are required")
