@@ -121,25 +121,29 @@ class ClockSampler:
 
 # ------------------------------------------------------------- workloads --
 
-def make_inputs_u32(n: int, device):
-    """The four distributions as device tensors (int32 views of uint32)."""
+def make_inputs_u32(n: int, device, dists=DISTS):
+    """The distributions as device tensors (int32 views of uint32)."""
     import numpy as np
     import torch
 
     import workloads as W
 
     out = {}
-    uni = W.uniform_u32(n, DIST_SEED["uniform"])
-    out["uniform"] = torch.from_numpy(uni.view(np.int32)).to(device)
-    # "sorted" / "reverse" are the seed-3 uniform draw ordered; sorting the
-    # draw on the GPU gives the same bytes as workloads.sorted_u32, faster.
-    draw = torch.from_numpy(W.uniform_u32(n, DIST_SEED["sorted"]).astype(np.int64)).to(device)
-    srt = torch.sort(draw).values
-    out["sorted"] = srt.to(torch.int32)  # values < 2^32 wrap to the int32 view of the uint32 bits
-    draw = torch.from_numpy(W.uniform_u32(n, DIST_SEED["reverse"]).astype(np.int64)).to(device)
-    out["reverse"] = torch.flip(torch.sort(draw).values, [0]).to(torch.int32)
-    del draw, srt
-    out["distinct16"] = torch.from_numpy(W.distinct16_u32(n, DIST_SEED["distinct16"]).view(np.int32)).to(device)
+    if "uniform" in dists:
+        uni = W.uniform_u32(n, DIST_SEED["uniform"])
+        out["uniform"] = torch.from_numpy(uni.view(np.int32)).to(device)
+    # "sorted" / "reverse" are a uniform draw ordered; sorting the draw on the
+    # GPU gives the same bytes as workloads.sorted_u32 / reverse_u32, faster.
+    for d in ("sorted", "reverse"):
+        if d in dists:
+            draw = torch.from_numpy(W.uniform_u32(n, DIST_SEED[d]).astype(np.int64)).to(device)
+            srt = torch.sort(draw).values
+            if d == "reverse":
+                srt = torch.flip(srt, [0])
+            out[d] = srt.to(torch.int32)  # values < 2^32 wrap to the int32 view of the uint32 bits
+            del draw, srt
+    if "distinct16" in dists:
+        out["distinct16"] = torch.from_numpy(W.distinct16_u32(n, DIST_SEED["distinct16"]).view(np.int32)).to(device)
     return out
 
 
@@ -186,10 +190,11 @@ def bench_plain(args, sq, dist, rank, world, local):
 
     dev = torch.device("cuda", local)
     n = args.n
-    inputs = make_inputs_u32(n, dev)
+    dists = args.dists.split(",")
+    inputs = make_inputs_u32(n, dev, dists)
     iota = torch.arange(n, dtype=torch.int32, device=dev)
     total = args.warmup + args.steps
-    seq = [DISTS[i % 4] for i in range(total)]
+    seq = [dists[i % len(dists)] for i in range(total)]
     keys = [inputs[d].clone() for d in seq]
     vals = [iota.clone() for _ in seq]
     torch.cuda.synchronize()
@@ -259,8 +264,9 @@ def bench_plain(args, sq, dist, rank, world, local):
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": workload_name, "n": n, "view": f"{int(n ** 0.5)}x{int(n ** 0.5)}",
-                   "key": "uint32", "payload": "uint32 original index", "distributions": DISTS,
-                   "distribution_seeds": DIST_SEED, "step_cycle": "step i sorts distribution i mod 4",
+                   "key": "uint32", "payload": "uint32 original index", "distributions": dists,
+                   "distribution_seeds": {d: DIST_SEED[d] for d in dists},
+                   "step_cycle": f"step i sorts distribution i mod {len(dists)}",
                    "cutoff": sq.get_cutoff("u32") if not cutoff else cutoff,
                    "l2": "inputs larger than L2 (each step sorts its own 2 GiB copy)",
                    "parallelism": f"replicas x{world}"},
@@ -283,10 +289,11 @@ def bench_e2e(sq, n, steps, dev, inputs):
     hk = torch.empty(n, dtype=torch.int32).pin_memory()
     hv = torch.empty(n, dtype=torch.int32).pin_memory()
     iota = torch.arange(n, dtype=torch.int32)
-    src = {d: inputs[d].cpu() for d in DISTS[:steps]}
+    names = list(inputs)
+    src = {d: inputs[d].cpu() for d in names[:steps]}
     tot = 0.0
     for i in range(steps):
-        d = DISTS[i % 4]
+        d = names[i % len(names)]
         hk.copy_(src[d])
         hv.copy_(iota)
         torch.cuda.synchronize()
@@ -532,6 +539,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--dists", default=",".join(DISTS), help="comma-separated subset (profiling runs)")
     ap.add_argument("--serve-requests", type=int, default=512)
     args = ap.parse_args()
     if args.warmup < 3:
