@@ -214,7 +214,8 @@ struct Engine {
     P.meta_cap = (u64)((double)total_n * (1.0 / kCountCols + 1.0 / kSkewBkts) +
                        (6.0 + kw) * ((double)total_n / std::sqrt((double)cutoff + 1) + P.ready_cap)) +
                  32 * P.ready_cap + 4096;
-    if (skew_only) {
+    if (skew_only) {  // one node, no leaves, no children
+      for (int c = 0; c < kLeafClasses; c++) P.leaf_cap[c] = 0;
       P.node_cap = 1;
       P.ready_cap = P.fresh_cap = 1;
       P.meta_cap = meta_layout(k, cols, (cols + kCountCols - 1) / kCountCols, (k + kSkewBkts - 1) / kSkewBkts,
