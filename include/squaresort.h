@@ -111,6 +111,25 @@ typedef struct {
 /* rows >= 1, cols >= 1, n <= rows*cols, n < 2^32. */
 sq_status sq_skew_transpose(const sq_skew_buf *buf, uint64_t rows, uint64_t cols, sq_stream_t stream);
 
+/* sq_skew_transpose without any device allocation.  The paper has no
+ * counterpart: this is for callers that cannot allocate device memory where
+ * they need the permutation -- a process whose frameworks already hold the
+ * whole device in their own caching pools, or a latency-critical path that
+ * must not call cudaMalloc / cudaFree (they can synchronise the device or
+ * fail under memory pressure).  Same arguments, results and errors as
+ * sq_skew_transpose; all scratch (per-node metadata, work lists, status
+ * words) comes from one 64 MiB array that the library holds in device memory
+ * on every GPU that loads it, until the process exits.  Shapes whose scratch
+ * exceeds 64 MiB (about 0.078 * k * cols + 2 * (k + cols) 32-bit words, e.g.
+ * beyond roughly 14000 x 14000 with k = cols) are refused with
+ * SQ_ERR_INVALID and a message naming the size.  The first call on a device
+ * looks up the array's device address (with that device current); make that
+ * first call before any stream capture.  Every call uses the same array and
+ * leaves the previous call's contents behind (the call initialises what it
+ * reads): calls whose GPU work overlaps -- on different streams or from
+ * different threads -- race on it and must be serialised by the caller. */
+sq_status sq_skew_transpose_noalloc(const sq_skew_buf *buf, uint64_t rows, uint64_t cols, sq_stream_t stream);
+
 /* One instance of a batched sort: device buffers, sorted in place. */
 typedef struct {
   void *keys;

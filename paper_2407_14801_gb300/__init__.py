@@ -70,6 +70,7 @@ def _bind(lib):
         "sq_sort": (i32, [vp, vp, u64, i32, u64, vp]),
         "sq_sort_ex": (i32, [vp, vp, u64, i32, u64, vp, ctypes.POINTER(SortOpts)]),
         "sq_skew_transpose": (i32, [ctypes.POINTER(SkewBuf), u64, u64, vp]),
+        "sq_skew_transpose_noalloc": (i32, [ctypes.POINTER(SkewBuf), u64, u64, vp]),
         "sq_sort_batch": (i32, [ctypes.POINTER(SortDesc), u32, vp]),
         "sq_serve_create": (i32, [ctypes.POINTER(vp), u64, ctypes.POINTER(ServeOpts)]),
         "sq_serve_submit": (i32, [vp, ctypes.POINTER(SortDesc), ctypes.POINTER(u64)]),
@@ -178,6 +179,20 @@ def sq_skew_transpose(keys_in, vals_in, rows: int, cols: int, pivot_keys, pivot_
 
 
 skew_transpose = sq_skew_transpose
+
+
+def sq_skew_transpose_noalloc(keys_in, vals_in, rows: int, cols: int, pivot_keys, pivot_vals, k: int, keys_out,
+                              vals_out, bucket_start_out, dtype: str | None = None, stream=None):
+    """sq_skew_transpose with its scratch in the library's fixed 64 MiB
+    device array instead of freshly allocated memory (for callers that cannot
+    allocate device memory there).  Calls whose GPU work overlaps race on that
+    array."""
+    buf = SkewBuf(_dtype_of(keys_in, dtype), _numel(keys_in), _ptr(keys_in), _ptr(vals_in), _ptr(keys_out),
+                  _ptr(vals_out), _ptr(pivot_keys), _ptr(pivot_vals), k, _ptr(bucket_start_out))
+    _check(lib().sq_skew_transpose_noalloc(ctypes.byref(buf), rows, cols, _stream(stream)))
+
+
+skew_transpose_noalloc = sq_skew_transpose_noalloc
 
 
 def sq_sort_batch(items, stream=None):

@@ -246,6 +246,11 @@ struct Engine {
     return P;
   }
 
+  static u64 skew_scratch_bytes(u64 n, u32 cols, u32 k) {
+    const Plan P = make_plan(n, 1, 2, 0, 1, k, cols);
+    return ((P.slab_bytes + 255) & ~(u64)255) + ((sizeof(Node) + 255) & ~(u64)255);
+  }
+
   static u64 scratch_bytes(u64 total_n, u32 ninst, u32 cutoff) {
     const Plan P = make_plan(total_n, ninst, cutoff, 0, 0, 0, 0);
     return P.slab_bytes + sizeof(Node) * P.node_cap + 4096;
@@ -442,14 +447,15 @@ struct Engine {
       Counters cnt;
       Status status;
     };
-    Readback *hrb = nullptr;
-    SQ_CU(cudaMallocHost((void **)&hrb, sizeof(Readback)));
+    static_assert(sizeof(Readback) <= 512, "read-back buffer contract");
+    Readback *hrb = reinterpret_cast<Readback *>(spec.host_readback);
+    if (!hrb) SQ_CU(cudaMallocHost((void **)&hrb, sizeof(Readback)));
     struct FreeHost {
       Readback *p;
       ~FreeHost() {
         if (p) cudaFreeHost(p);
       }
-    } fh{hrb};
+    } fh{spec.host_readback ? nullptr : hrb};
     Counters cur_cnt = hc[0];
     u32 done = hs.done;
     int rc = 0;

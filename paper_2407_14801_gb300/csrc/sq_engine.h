@@ -63,7 +63,13 @@ struct RunSpec {
   void *(*dev_alloc)(void *ctx, size_t bytes);
   void (*dev_free)(void *ctx, void *p);
   void *alloc_ctx;
+  // Optional host buffer (any memory, >= 512 bytes) for the per-round
+  // read-back; default: pinned memory from cudaMallocHost.
+  void *host_readback;
 };
+
+// Device scratch bytes (slab + node record) of a stand-alone SkewTranspose.
+uint64_t engine_skew_scratch_bytes(int dtype, uint64_t n, uint64_t cols, uint64_t k);
 
 // Upper bound of the engine's own scratch bytes for a run (admission control).
 uint64_t engine_scratch_bytes(int dtype, uint64_t total_n, uint32_t ninst, uint32_t cutoff);
