@@ -104,30 +104,15 @@ struct Engine {
     return cudaGetLastError();
   }
 
-  template <int T, int R>
-  static cudaError_t launch_leaf_radix(Launcher &L, const Ctx &c, int cls, u32 count) {
-    const size_t smem = RadixSorter<K, T, R>::kSmem;
-    auto kern = k_leaf_radix<DT, T, R>;
-    cudaError_t e = set_smem(kern, smem);
-    if (e != cudaSuccess) return e;
-    L.begin(KF_LEAF);
-    kern<<<count, T, smem, L.st>>>(c, cls, count);
-    L.end();
-    return cudaGetLastError();
-  }
-
-  template <int T, int R, int G, bool RADIX>
-  static cudaError_t launch_leaf_cluster(Launcher &L, const Ctx &c, int cls, u32 count) {
-    const size_t smem = RADIX ? RadixSorter<K, T, R>::kSmem : sizeof(E) * (size_t)Sorter<K, T, R, false>::SMEM;
-    auto kern = k_leaf_cluster<DT, T, R, G, RADIX>;
-    cudaError_t e = set_smem(kern, smem);
-    if (e != cudaSuccess) return e;
+  template <class Kern, class... Args>
+  static cudaError_t launch_cluster(Kern kern, dim3 grid, int T, size_t smem, int G, cudaStream_t st,
+                                    Args... args) {
     cudaLaunchConfig_t cfg;
     memset(&cfg, 0, sizeof(cfg));
-    cfg.gridDim = dim3(count * G, 1, 1);
+    cfg.gridDim = grid;
     cfg.blockDim = dim3(T, 1, 1);
     cfg.dynamicSmemBytes = smem;
-    cfg.stream = L.st;
+    cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = G;
@@ -135,10 +120,37 @@ struct Engine {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    L.begin(KF_LEAF);
-    e = cudaLaunchKernelEx(&cfg, kern, c, cls, count);
-    L.end();
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, args...);
     return e != cudaSuccess ? e : cudaGetLastError();
+  }
+
+  template <int T, int R, int G>
+  static cudaError_t launch_leaf_radix(Launcher &L, const Ctx &c, int cls, u32 count) {
+    const size_t smem = RadixSorter<K, T, R, G>::kSmem;
+    auto kern = k_leaf_radix<DT, T, R, G>;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    L.begin(KF_LEAF);
+    if (G == 1) {
+      kern<<<count, T, smem, L.st>>>(c, cls, count);
+      e = cudaGetLastError();
+    } else {
+      e = launch_cluster(kern, dim3(count * G, 1, 1), T, smem, G, L.st, c, cls, count);
+    }
+    L.end();
+    return e;
+  }
+
+  template <int T, int R, int G>
+  static cudaError_t launch_leaf_cluster(Launcher &L, const Ctx &c, int cls, u32 count) {
+    const size_t smem = sizeof(E) * (size_t)Sorter<K, T, R, false>::SMEM;
+    auto kern = k_leaf_cluster<DT, T, R, G>;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    L.begin(KF_LEAF);
+    e = launch_cluster(kern, dim3(count * G, 1, 1), T, smem, G, L.st, c, cls, count);
+    L.end();
+    return e;
   }
 
   static cudaError_t launch_leaf_class(Launcher &L, const Ctx &c, int cls, u32 count) {
@@ -146,17 +158,31 @@ struct Engine {
       case 0: return launch_leaf<32, 2, true>(L, c, 0, count);
       case 1: return launch_leaf<32, 16, true>(L, c, 1, count);
       case 2: return launch_leaf<128, 16, false>(L, c, 2, count);
-      case 3: return launch_leaf_radix<512, 16>(L, c, 3, count);
+      case 3: return launch_leaf_radix<512, 16, 1>(L, c, 3, count);
       case 4:
-        if constexpr (sizeof(E) == 8) return launch_leaf_radix<512, 32>(L, c, 4, count);
-        else return launch_leaf_cluster<512, 16, 2, true>(L, c, 4, count);
+        if constexpr (sizeof(E) == 8) return launch_leaf<1024, 16, false>(L, c, 4, count);
+        else return launch_leaf_cluster<512, 16, 2>(L, c, 4, count);
       case 5:
-        if constexpr (sizeof(E) == 8) return launch_leaf_cluster<1024, 16, 2, false>(L, c, 5, count);
-        else return launch_leaf_cluster<512, 16, 4, true>(L, c, 5, count);
+        if constexpr (sizeof(E) == 8) return launch_leaf_cluster<1024, 16, 2>(L, c, 5, count);
+        else return launch_leaf_cluster<512, 16, 4>(L, c, 5, count);
       default:
-        if constexpr (sizeof(E) == 8) return launch_leaf_cluster<1024, 16, 4, false>(L, c, 6, count);
-        else return launch_leaf_cluster<512, 16, 8, true>(L, c, 6, count);
+        if constexpr (sizeof(E) == 8) return launch_leaf_cluster<1024, 16, 4>(L, c, 6, count);
+        else return launch_leaf_cluster<512, 16, 8>(L, c, 6, count);
     }
+  }
+
+  // The (key, val) merge sort of leaves whose radix check failed this round.
+  static cudaError_t launch_fixup(Launcher &L, const Ctx &c, int nsm) {
+    constexpr bool wide = sizeof(E) == 8;
+    constexpr int T = wide ? 1024 : 512, R = 16, G = wide ? 4 : 8;
+    const size_t smem = sizeof(E) * (size_t)Sorter<K, T, R, false>::SMEM;
+    auto kern = k_fixup<DT, T, R, G>;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    L.begin(KF_AUX);
+    e = launch_cluster(kern, dim3(std::max(1, nsm / G) * G, 1, 1), T, smem, G, L.st, c);
+    L.end();
+    return e;
   }
 
   template <int T, int R, bool WARP>
@@ -189,7 +215,8 @@ struct Engine {
     u32 leaf_cap[kLeafClasses];
     u64 ready_cap, fresh_cap, node_cap, meta_cap;
     size_t o_inst, o_leaves[2][kLeafClasses], o_ready[2], o_fresh[2], o_cnt, o_status, o_meta, o_done, o_trace,
-        o_wbase;
+        o_wbase, o_fix;
+    u64 fix_cap;
     size_t slab_bytes;
   };
 
@@ -242,6 +269,9 @@ struct Engine {
     P.o_done = carve(4 * (size_t)std::max<u32>(ninst, 1));
     P.o_trace = carve(sizeof(TraceRec) * (size_t)trace_cap);
     P.o_wbase = carve(4 * 4 * P.ready_cap);
+    P.fix_cap = 0;
+    for (int c = 3; c < kLeafClasses; c++) P.fix_cap += P.leaf_cap[c];
+    P.o_fix = carve(sizeof(Leaf) * (size_t)P.fix_cap);
     P.slab_bytes = off;
     return P;
   }
@@ -328,6 +358,8 @@ struct Engine {
     for (int cl = 0; cl < kLeafClasses; cl++) c.leaf_cap[cl] = leaf_cap[cl];
     c.ready_cap = (u32)ready_cap;
     c.wbase = (u32 *)(slab + o_wbase);
+    c.fix = (Leaf *)(slab + P.o_fix);
+    c.fix_cap = (u32)std::min<u64>(P.fix_cap, 0xffffffffull);
     c.fresh_cap = (u32)fresh_cap;
     c.status = (Status *)(slab + o_status);
     c.meta = (u32 *)(slab + o_meta);
@@ -482,13 +514,16 @@ struct Engine {
       c.cnt_cur = cnt + cur;
       c.cnt_nxt = cnt + nxt;
       SQ_CU(cudaMemsetAsync(cnt + nxt, 0, sizeof(Counters), st));
-      SQ_CU(cudaMemsetAsync(&c.status->cur_count, 0, 5 * sizeof(u32), st));
+      SQ_CU(cudaMemsetAsync(&c.status->cur_count, 0, 7 * sizeof(u32), st));
       // leaves (simple_sort)
+      bool radix_leaves = false;
       for (int cl = 0; cl < NCLASS; cl++) {
         if (!cur_cnt.leaves[cl]) continue;
         L.local.bytes[KF_LEAF] += 2.0 * (KEY_BYTES + 4) * (double)cur_cnt.leaf_elems[cl];
         SQ_CU(launch_leaf_class(L, c, cl, cur_cnt.leaves[cl]));
+        radix_leaves |= cl == 3;
       }
+      if (radix_leaves) SQ_CU(launch_fixup(L, c, nsm));
       // nodes whose columns are sorted: pivots, counts, SkewTranspose, buckets
       const u32 ready = cur_cnt.ready;
       if (ready) {

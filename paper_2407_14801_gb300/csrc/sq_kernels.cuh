@@ -27,8 +27,9 @@ template <int DT>
 struct LeafCfg;
 // Leaf classes (elements per class): c0 = warp x 2 (64), c1 = warp x 16
 // (512), c2 = 128 x 16 (2048), c3 = 512 x 16 (8192), c4 = 16384, c5 = 32768,
-// c6 = 65536.  c4..c6 are one CTA of 512 x 32 and clusters of 2 and 4 CTAs
-// of 1024 x 16 (uint32 keys), or clusters of 2, 4 and 8 CTAs of 512 x 16.  Pivot samples use the single-CTA sorters only.
+// c6 = 65536.  c3 is a radix sort on one CTA of 512 x 16; c4..c6 are merge
+// sorts on one CTA of 1024 x 16 and clusters of 2 and 4 of them (uint32
+// keys), or on clusters of 2, 4 and 8 CTAs of 512 x 16.  Pivot samples use the single-CTA sorters only.
 template <>
 struct LeafCfg<DT_U32> {
   static constexpr int nclass = 7;
@@ -179,39 +180,61 @@ __device__ __forceinline__ void grab_item(const Ctx &c, u32 *cursor, u32 total, 
 }
 
 // ------------------------------------------------------------ radix leaf ---
-// Leaf sort for one CTA: a stable least-significant-digit radix sort of the
-// key ordinals (8-bit digits, one pass per key byte) in shared memory.  Each
-// pass ranks the elements warp by warp (peers with the same digit found by
-// __match_any_sync, in sequence order), forms digit-major / warp-minor
-// offsets with one block scan, and scatters.  A stable key sort equals the
-// (key, val) order exactly when, among equal keys, vals already increase
-// with position -- true at every level of the recursion when vals are the
-// original index; the result is checked and, if the check fails, the CTA
-// sorts the leaf again with the (key, val) merge sort.
-template <class K, int T, int R>
+// Leaf sort by a stable least-significant-digit radix sort of the key
+// ordinals (8-bit digits, one pass per key byte), on one CTA (G = 1) or on a
+// cluster of G CTAs whose shared memories hold consecutive parts of the leaf.
+// A pass ranks every CTA's elements warp by warp (peers with the same digit
+// found by __match_any_sync, in sequence order, one shared atomic per digit
+// group), adds the per-digit totals of the lower-ranked CTAs (read through
+// distributed shared memory) and of the lower digits, and scatters each
+// element straight into the shared memory of the CTA that owns its new
+// position.  A stable key sort equals the (key, val) order exactly when,
+// among equal keys, vals already increase with position -- true at every
+// level of the recursion when vals are the original index.  The result is
+// checked; a leaf that fails is re-sorted by the (key, val) merge sort.
+template <class K, int T, int R, int G>
 struct RadixSorter {
   typedef typename K::key_t key_t;
   typedef typename K::elem_t E;
-  typedef Sorter<K, T, R, false> MS;
   static constexpr int W = T / 32;
-  static constexpr int N = T * R;
+  static constexpr int NC = T * R;  // elements per CTA
   static constexpr int RADIX = 256;
   static constexpr int PASSES = (int)sizeof(typename K::ord_t);
   static constexpr int CS = W + 1;  // padded counter row: (digit, warp) at d*CS + w
-  static constexpr size_t kValsOff = sizeof(key_t) * (size_t)N;
-  static constexpr size_t kCntOff = kValsOff + 4 * (size_t)N;
-  static constexpr size_t kScanOff = kCntOff + 4 * (size_t)RADIX * CS;
-  static constexpr size_t kRadixBytes = kScanOff + 4 * 40;
-  static constexpr size_t kMergeBytes = sizeof(E) * (size_t)MS::SMEM;
-  static constexpr size_t kSmem = kRadixBytes > kMergeBytes ? kRadixBytes : kMergeBytes;
-  static_assert(R % 2 == 0 && T % 256 == 0, "ranks are packed in pairs; 8 counters per thread");
+  static constexpr size_t kValsOff = sizeof(key_t) * (size_t)NC;
+  static constexpr size_t kCntOff = kValsOff + 4 * (size_t)NC;
+  static constexpr size_t kTotOff = kCntOff + 4 * (size_t)RADIX * CS;
+  static constexpr size_t kBaseOff = kTotOff + 4 * (size_t)RADIX;
+  static constexpr size_t kScanOff = kBaseOff + 4 * (size_t)RADIX;
+  static constexpr size_t kFlagOff = kScanOff + 4 * 40;
+  static constexpr size_t kSmem = kFlagOff + 16;
+  static_assert(R % 4 == 0 && T >= RADIX && T % 32 == 0, "one thread per digit; ranks and digits packed");
 
   __device__ __forceinline__ static u32 digit(key_t k, int pass) {
     return (u32)((u64)K::ord_key(k) >> (8 * pass)) & (RADIX - 1);
   }
   __device__ __forceinline__ static int striped(int tid, int q) { return (tid >> 5) * (R * 32) + q * 32 + (tid & 31); }
+  __device__ __forceinline__ static int rank_in_cluster() {
+    if constexpr (G > 1)
+      return (int)cooperative_groups::this_cluster().block_rank();
+    else
+      return 0;
+  }
+  __device__ __forceinline__ static void cluster_sync() {
+    if constexpr (G > 1)
+      cooperative_groups::this_cluster().sync();
+    else
+      __syncthreads();
+  }
+  template <class P>
+  __device__ __forceinline__ static P *peer(P *p, int r) {
+    if constexpr (G > 1)
+      return cooperative_groups::this_cluster().map_shared_rank(p, r);
+    else
+      return p;
+  }
 
-  // Loads n <= N elements into the warp-striped register layout (coalesced).
+  // Loads this CTA's part (n elements) into the warp-striped register layout.
   __device__ static void load(key_t (&kx)[R], u32 (&vx)[R], int tid, const key_t *keys, const u32 *vals, u32 n) {
 #pragma unroll
     for (int q = 0; q < R; q++) {
@@ -222,25 +245,33 @@ struct RadixSorter {
     }
   }
 
-  // Sorts; the result is left in shared memory (keys at 0, vals at
-  // kValsOff).  Returns whether [0, n) is in (key, val) order.
+  // Sorts the G*NC elements (the leaf's first n are real); afterwards CTA r
+  // holds sorted positions [r*NC, (r+1)*NC) in its shared memory.  Returns
+  // whether the leaf is in (key, val) order (same answer in every CTA).
   __device__ static bool sort(key_t (&kx)[R], u32 (&vx)[R], unsigned char *smem, int tid, u32 n) {
     key_t *sk = reinterpret_cast<key_t *>(smem);
     u32 *sv = reinterpret_cast<u32 *>(smem + kValsOff);
     u32 *cnt = reinterpret_cast<u32 *>(smem + kCntOff);
+    u32 *tot = reinterpret_cast<u32 *>(smem + kTotOff);
+    u32 *base = reinterpret_cast<u32 *>(smem + kBaseOff);
     u32 *scan = reinterpret_cast<u32 *>(smem + kScanOff);
-    const int lane = tid & 31, w = tid >> 5;
+    u32 *flag = reinterpret_cast<u32 *>(smem + kFlagOff);
+    const int lane = tid & 31, w = tid >> 5, rank = rank_in_cluster();
     const u32 lt = (1u << lane) - 1u;
 #pragma unroll 1
     for (int pass = 0; pass < PASSES; pass++) {
       for (int i = tid; i < RADIX * CS; i += T) cnt[i] = 0;
       __syncthreads();
-      u32 rk[R / 2];
+      u32 rk[R / 2], dg[R / 4];  // ranks (2 x 16 bits) and digits (4 x 8 bits) per register
 #pragma unroll
       for (int q = 0; q < R; q++) {
         // rank among this warp's elements with the same digit, in sequence
         // order: the lowest peer reserves the group's slots, all read its base
         const u32 d = digit(kx[q], pass);
+        if (q & 3)
+          dg[q >> 2] |= d << ((q & 3) * 8);
+        else
+          dg[q >> 2] = d;
         const u32 peers = __match_any_sync(0xffffffffu, d);
         const u32 before = __popc(peers & lt);
         const int leader = __ffs(peers) - 1;
@@ -254,34 +285,44 @@ struct RadixSorter {
           rk[q >> 1] = r;
       }
       __syncthreads();
-      // exclusive scan of the counters in (digit, warp) order, 8 per thread
-      {
-        const int f0 = tid * 8;
-        u32 loc[8], sum = 0;
-#pragma unroll
-        for (int i = 0; i < 8; i++) {
-          const int f = f0 + i, d = f / W, ww = f - d * W;
-          loc[i] = cnt[d * CS + ww];
-          sum += loc[i];
+      if (tid < RADIX) {  // per digit: offsets of this CTA's warps, and its total
+        u32 run = 0;
+        for (int ww = 0; ww < W; ww++) {
+          const u32 c = cnt[tid * CS + ww];
+          cnt[tid * CS + ww] = run;
+          run += c;
         }
-        u32 tot;
-        u32 run = block_excl_scan_u32(sum, scan, tot);
+        tot[tid] = run;
+      }
+      cluster_sync();
+      u32 all = 0, lower = 0;
+      if (tid < RADIX) {  // this digit over the cluster, and over lower-ranked CTAs
 #pragma unroll
-        for (int i = 0; i < 8; i++) {
-          const int f = f0 + i, d = f / W, ww = f - d * W;
-          cnt[d * CS + ww] = run;
-          run += loc[i];
+        for (int r = 0; r < G; r++) {
+          const u32 v = (r == rank) ? tot[tid] : *peer(tot + tid, r);
+          all += v;
+          if (r < rank) lower += v;
         }
       }
+      u32 digits_total;
+      const u32 ex = block_excl_scan_u32(all, scan, digits_total);
+      if (tid < RADIX) base[tid] = ex + lower;
       __syncthreads();
 #pragma unroll
       for (int q = 0; q < R; q++) {
-        const u32 d = digit(kx[q], pass);
-        const u32 pos = cnt[d * CS + w] + ((rk[q >> 1] >> ((q & 1) * 16)) & 0xffffu);
-        sk[pos] = kx[q];
-        sv[pos] = vx[q];
+        const u32 d = (dg[q >> 2] >> ((q & 3) * 8)) & 0xffu;
+        const u32 pos = base[d] + cnt[d * CS + w] + ((rk[q >> 1] >> ((q & 1) * 16)) & 0xffffu);
+        const int owner = G > 1 ? (int)(pos / NC) : 0;
+        const u32 lp = G > 1 ? pos - (u32)owner * NC : pos;
+        if (G == 1 || owner == rank) {
+          sk[lp] = kx[q];
+          sv[lp] = vx[q];
+        } else {
+          *peer(sk + lp, owner) = kx[q];
+          *peer(sv + lp, owner) = vx[q];
+        }
       }
-      __syncthreads();
+      cluster_sync();
       if (pass + 1 < PASSES) {
 #pragma unroll
         for (int q = 0; q < R; q++) {
@@ -291,56 +332,65 @@ struct RadixSorter {
         }
       }
     }
-    // (key, val) order check over [0, n)
+    // (key, val) order check over the leaf's first n positions
     bool bad = false;
+    const u32 g0 = (u32)rank * NC;
 #pragma unroll 4
     for (int q = 0; q < R; q++) {
       const u32 i = (u32)tid * R + q;
-      if (i + 1 < n && K::ord_key(sk[i]) == K::ord_key(sk[i + 1]) && sv[i] > sv[i + 1]) bad = true;
+      const u32 gi = g0 + i;
+      if (gi + 1 < n) {
+        key_t k1;
+        u32 v1;
+        if (i + 1 < (u32)NC) {
+          k1 = sk[i + 1];
+          v1 = sv[i + 1];
+        } else {
+          k1 = *peer(sk, rank + 1);
+          v1 = *peer(sv, rank + 1);
+        }
+        if (K::ord_key(sk[i]) == K::ord_key(k1) && sv[i] > v1) bad = true;
+      }
     }
-    return !__syncthreads_or(bad);
-  }
-
-  // Blocked register copy of the sorted smem contents (for merges).
-  __device__ static void to_blocked(E (&x)[R], unsigned char *smem, int tid) {
-    const key_t *sk = reinterpret_cast<const key_t *>(smem);
-    const u32 *sv = reinterpret_cast<const u32 *>(smem + kValsOff);
+    bad = __syncthreads_or(bad);
+    if constexpr (G == 1) {
+      return !bad;
+    } else {
+      if (tid == 0) *flag = bad ? 1u : 0u;
+      cluster_sync();
+      u32 any = 0;
 #pragma unroll
-    for (int q = 0; q < R; q++) x[q] = K::make(sk[tid * R + q], sv[tid * R + q]);
-    __syncthreads();
+      for (int r = 0; r < G; r++) any |= *peer(flag, r);
+      cluster_sync();  // peers' flags read before anyone leaves or reuses them
+      return any == 0;
+    }
   }
 
-  // Coalesced store of the first n sorted elements from shared memory.
-  __device__ static void store(unsigned char *smem, int tid, key_t *keys, u32 *vals, u32 n) {
+  // Coalesced store of this CTA's part (its first nr positions).
+  __device__ static void store(unsigned char *smem, int tid, key_t *keys, u32 *vals, u32 nr) {
     const key_t *sk = reinterpret_cast<const key_t *>(smem);
     const u32 *sv = reinterpret_cast<const u32 *>(smem + kValsOff);
 #pragma unroll
     for (int q = 0; q < R; q++) {
       const int p = q * T + tid;
-      if ((u32)p < n) {
+      if ((u32)p < nr) {
         keys[p] = sk[p];
         vals[p] = sv[p];
       }
     }
   }
-
-  // The whole leaf: radix sort, check, merge-sort fallback, store.
-  __device__ static void sort_leaf(unsigned char *smem, int tid, const key_t *ik, const u32 *iv, key_t *okk,
-                                   u32 *ov, u32 n) {
-    key_t kx[R];
-    u32 vx[R];
-    load(kx, vx, tid, ik, iv, n);
-    if (sort(kx, vx, smem, tid, n)) {
-      store(smem, tid, okk, ov, n);
-    } else {
-      E x[R];
-      to_blocked(x, smem, tid);
-      E *s = reinterpret_cast<E *>(smem);
-      MS::sort(x, s, tid);
-      MS::store(x, s, tid, okk, ov, n);
-    }
-  }
 };
+
+// Appends a leaf whose radix result failed the (key, val) check; it is
+// sorted again, in place in its output buffer, by k_fixup later this round.
+__device__ __forceinline__ void push_fix(const Ctx &c, Leaf L) {
+  const u32 i = atomicAdd(&c.status->fix_count, 1u);
+  L.flags |= LEAF_IN_OUT;
+  if (i < c.fix_cap)
+    c.fix[i] = L;
+  else
+    atomicOr(&c.status->error, ERRB_LIST);
+}
 
 // A finished unit of work (leaf or completed node) reports to its parent.
 static __device__ void child_done(const Ctx &c, u32 parent, u32 kind, u32 inst) {
@@ -400,30 +450,45 @@ __global__ void __launch_bounds__(WARP ? 256 : T) k_leaf(Ctx c, int cls, u32 cou
   }
 }
 
-// A leaf of a one-CTA class, radix-sorted (see RadixSorter).
-template <int DT, int T, int R>
-__global__ void __launch_bounds__(T, (R <= 16 && sizeof(typename KT<DT>::elem_t) == 8) ? 2 : 1) k_leaf_radix(Ctx c, int cls, u32 count) {
+// A leaf of a radix class: one CTA (G = 1) or a cluster of G CTAs, CTA
+// `rank` holding positions [rank*NC, (rank+1)*NC) of the leaf.
+#ifndef SQ_RADIX_MINBLOCKS
+#define SQ_RADIX_MINBLOCKS 2  // CTAs per SM the 8-byte-element radix kernels are built for
+#endif
+template <int DT, int T, int R, int G>
+__global__ void __launch_bounds__(T, sizeof(typename KT<DT>::elem_t) == 8 ? SQ_RADIX_MINBLOCKS : 1)
+    k_leaf_radix(Ctx c, int cls, u32 count) {
   typedef KT<DT> K;
-  typedef RadixSorter<K, T, R> RS;
+  typedef RadixSorter<K, T, R, G> RS;
   typedef typename K::key_t key_t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const u32 li = blockIdx.x;
-  if (li >= count) return;
+  const u32 li = blockIdx.x / G;
+  if (li >= count) return;  // the whole cluster
+  const int tid = threadIdx.x, rank = RS::rank_in_cluster();
   const Leaf L = c.leaves_cur[cls][li];
   const Inst I = c.inst[L.inst];
-  const u32 out = L.flags >> 8;
-  RS::sort_leaf(smem_raw, threadIdx.x, (const key_t *)I.keys + L.off, I.vals + L.off,
-                (key_t *)(out ? I.dkeys : I.keys) + L.off, (out ? I.dvals : I.vals) + L.off, L.n);
-  __syncthreads();
-  if (threadIdx.x == 0) {
+  const u64 off = L.off + (u64)rank * RS::NC;
+  const u32 nr = L.n > (u32)rank * RS::NC ? min((u32)RS::NC, L.n - (u32)rank * RS::NC) : 0u;
+  const u32 out = (L.flags >> 8) & 0xffu;
+  key_t kx[R];
+  u32 vx[R];
+  RS::load(kx, vx, tid, (const key_t *)I.keys + off, I.vals + off, nr);
+  const bool ok = RS::sort(kx, vx, smem_raw, tid, L.n);
+  RS::store(smem_raw, tid, (key_t *)(out ? I.dkeys : I.keys) + off, (out ? I.dvals : I.vals) + off, nr);
+  RS::cluster_sync();
+  if (rank == 0 && tid == 0) {
     __threadfence();
-    child_done(c, L.parent, L.flags & 0xffu, L.inst);
+    if (ok)
+      child_done(c, L.parent, L.flags & 0xffu, L.inst);
+    else
+      push_fix(c, L);
   }
 }
 
-// A leaf of a cluster class: CTA `rank` of the cluster loads, sorts and
-// stores elements [rank*NC, (rank+1)*NC) of the leaf; the cluster merges.
-template <int DT, int T, int R, int G, bool RADIX>
+// A leaf of a cluster merge class: CTA `rank` of the cluster loads and
+// sorts positions [rank*NC, (rank+1)*NC) of the leaf, then the cluster merges
+// through distributed shared memory (ClusterSorter).
+template <int DT, int T, int R, int G>
 __global__ void __launch_bounds__(T, 1) k_leaf_cluster(Ctx c, int cls, u32 count) {
   typedef KT<DT> K;
   typedef ClusterSorter<K, T, R, G> CS;
@@ -442,30 +507,55 @@ __global__ void __launch_bounds__(T, 1) k_leaf_cluster(Ctx c, int cls, u32 count
   const Inst I = c.inst[L.inst];
   const u64 off = L.off + (u64)rank * CS::NC;
   const u32 nr = L.n > (u32)rank * CS::NC ? min((u32)CS::NC, L.n - (u32)rank * CS::NC) : 0u;
-  // this CTA's part: radix sort (merge sort if the (key, val) check fails),
-  // then the cross-CTA merge rounds
-  typedef RadixSorter<K, T, R> RS;
   E x[R];
-  if constexpr (RADIX) {
-    key_t kx[R];
-    u32 vx[R];
-    RS::load(kx, vx, tid, (const key_t *)I.keys + off, I.vals + off, nr);
-    const bool ok = RS::sort(kx, vx, smem_raw, tid, nr);
-    RS::to_blocked(x, smem_raw, tid);
-    if (!ok) S::sort(x, s, tid);
-  } else {
-    S::load(x, s, tid, (const key_t *)I.keys + off, I.vals + off, nr);
-    S::sort(x, s, tid);
-  }
-  CS::merge_rounds(x, s, tid);
-  const u32 out = L.flags >> 8;
-  key_t *ok = (key_t *)(out ? I.dkeys : I.keys) + off;
-  u32 *ov = (out ? I.dvals : I.vals) + off;
-  S::store(x, s, tid, ok, ov, nr);
+  S::load(x, s, tid, (const key_t *)I.keys + off, I.vals + off, nr);
+  CS::sort(x, s, tid);
+  const u32 out = (L.flags >> 8) & 0xffu;
+  S::store(x, s, tid, (key_t *)(out ? I.dkeys : I.keys) + off, (out ? I.dvals : I.vals) + off, nr);
   cl.sync();
   if (rank == 0 && tid == 0) {
     __threadfence();
     child_done(c, L.parent, L.flags & 0xffu, L.inst);
+  }
+}
+
+// The (key, val) merge sort for leaves whose radix check failed: clusters of
+// G CTAs loop over the round's fix list; each leaf sits in its output buffer.
+template <int DT, int T, int R, int G>
+__global__ void __launch_bounds__(T, 1) k_fixup(Ctx c) {
+  typedef KT<DT> K;
+  typedef ClusterSorter<K, T, R, G> CS;
+  typedef typename CS::S S;
+  typedef typename K::elem_t E;
+  typedef typename K::key_t key_t;
+  namespace cg = cooperative_groups;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ u32 s_item;
+  E *s = reinterpret_cast<E *>(smem_raw);
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank(), tid = threadIdx.x;
+  for (;;) {
+    if (rank == 0 && tid == 0) s_item = atomicAdd(&c.status->cur_fix, 1u);
+    cl.sync();
+    const u32 item = *cl.map_shared_rank(&s_item, 0);
+    cl.sync();  // everyone has read the item before rank 0 grabs the next
+    if (item >= min(c.status->fix_count, c.fix_cap)) break;
+    const Leaf L = c.fix[item];
+    const Inst I = c.inst[L.inst];
+    const u32 out = (L.flags >> 8) & 0xffu;
+    key_t *kk = (key_t *)(out ? I.dkeys : I.keys) + L.off;
+    u32 *vv = (out ? I.dvals : I.vals) + L.off;
+    const u64 off = (u64)rank * CS::NC;
+    const u32 nr = L.n > (u32)off ? min((u32)CS::NC, L.n - (u32)off) : 0u;
+    E x[R];
+    S::load(x, s, tid, kk + off, vv + off, nr);
+    CS::sort(x, s, tid);
+    S::store(x, s, tid, kk + off, vv + off, nr);
+    cl.sync();
+    if (rank == 0 && tid == 0) {
+      __threadfence();
+      child_done(c, L.parent, L.flags & 0xffu, L.inst);
+    }
   }
 }
 

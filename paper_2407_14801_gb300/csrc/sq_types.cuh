@@ -191,8 +191,9 @@ struct Node {
 // A leaf: sorted in one group of threads (n <= cutoff).
 struct Leaf {
   u64 off;
-  u32 n, inst, parent, flags;  // flags: kind | out << 8
+  u32 n, inst, parent, flags;  // flags: kind | out << 8 | LEAF_IN_OUT
 };
+constexpr u32 LEAF_IN_OUT = 1u << 16;  // input already sits in the output buffer
 
 // Per-parity list counters (zeroed before the round that fills them).
 struct Counters {
@@ -213,8 +214,8 @@ struct Status {
   // per-round work totals written by the plan step
   u32 units, tiles, srows, echunks;
   u64 meta_words;
-  // persistent-kernel work cursors
-  u32 cur_count, cur_scan, cur_skew, cur_expand, cur_ebkt;
+  // persistent-kernel work cursors (zeroed every round, with fix_count)
+  u32 cur_count, cur_scan, cur_skew, cur_expand, cur_ebkt, cur_fix, fix_count;
   u32 pad;
 };
 
@@ -252,6 +253,8 @@ struct Ctx {
   TraceRec *trace;
   u32 trace_cap;
   u32 cutoff;
+  Leaf *fix;    // leaves whose radix result failed the (key, val) check this round
+  u32 fix_cap;
   u32 class_cap[kLeafClasses];  // max elements per leaf class
   int recurse;                  // 0 for a stand-alone SkewTranspose
 };
