@@ -492,7 +492,7 @@ struct Engine {
     u32 done = hs.done;
     int rc = 0;
     u64 rounds = 0;
-    const int grid_count = nsm * 2, grid_scan = nsm * 8, grid_skew = nsm * 4, grid_expand = nsm * 4;
+    const int grid_count = nsm * 2, grid_scan = nsm * 8, grid_skew = nsm * 5, grid_expand = nsm * 4;
     for (u32 r = 0;; r++) {
       const int cur = r & 1, nxt = cur ^ 1;
       if (!spec.skew_only && done >= ninst) break;

@@ -272,7 +272,16 @@ struct RadixSorter {
           dg[q >> 2] |= d << ((q & 3) * 8);
         else
           dg[q >> 2] = d;
+#if SQ_RADIX_BALLOT
+        u32 peers = 0xffffffffu;  // lanes whose digit equals mine, one ballot per digit bit
+#pragma unroll
+        for (int bit = 0; bit < 8; bit++) {
+          const u32 m = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+          peers &= ((d >> bit) & 1u) ? m : ~m;
+        }
+#else
         const u32 peers = __match_any_sync(0xffffffffu, d);
+#endif
         const u32 before = __popc(peers & lt);
         const int leader = __ffs(peers) - 1;
         u32 b = 0;
@@ -452,6 +461,9 @@ __global__ void __launch_bounds__(WARP ? 256 : T) k_leaf(Ctx c, int cls, u32 cou
 
 // A leaf of a radix class: one CTA (G = 1) or a cluster of G CTAs, CTA
 // `rank` holding positions [rank*NC, (rank+1)*NC) of the leaf.
+#ifndef SQ_RADIX_BALLOT
+#define SQ_RADIX_BALLOT 1  // peer masks from per-bit ballots rather than __match_any_sync
+#endif
 #ifndef SQ_RADIX_MINBLOCKS
 #define SQ_RADIX_MINBLOCKS 2  // CTAs per SM the 8-byte-element radix kernels are built for
 #endif
@@ -941,7 +953,6 @@ static __global__ void __launch_bounds__(1024) k_bstart(Ctx c, u32 ready_count, 
 template <int DT, int CAP>
 struct SkewSmem {
   typedef typename KT<DT>::elem_t E;
-  E in_e[CAP];
   E out_e[CAP];
   E piv[kSkewBkts];
   u32 base[kSkewBkts], running[kSkewBkts], tot[kSkewBkts], ob[kSkewBkts];
@@ -951,7 +962,7 @@ struct SkewSmem {
   u32 first[kSkewCols][kSkewBkts + 1];
   u32 last[kSkewCols][kSkewBkts + 1];
   uint16_t off[kSkewCols][kSkewBkts + 2];  // within a bucket: elements of lower columns
-  uint8_t in_j[CAP], in_c[CAP], out_j[CAP];
+  uint8_t in_j[CAP], out_j[CAP];
   u32 s_u, s_ri, s_S;
 };
 
@@ -1082,9 +1093,7 @@ __global__ void __launch_bounds__(256) k_skew(Ctx c, u32 ready_count) {
           const int nextb = __shfl_down_sync(0xffffffffu, jb, 1);
           if (valid) {
             const u32 ql = q - cs;
-            sm.in_e[ql] = e;
             sm.in_j[ql] = (uint8_t)jb;
-            sm.in_c[ql] = (uint8_t)ci;
             if (lane == 0 ? jb != carry_b : jb != prevb) atomicMin(&sm.first[ci][jb], ql);
             if (lane == lastv || nextb != jb) atomicMax(&sm.last[ci][jb], ql);
           }
@@ -1109,12 +1118,24 @@ __global__ void __launch_bounds__(256) k_skew(Ctx c, u32 ready_count) {
         sm.ob[2 * lane + 1] = ex + v0;
       }
       __syncthreads();
-      // 3. bucket-major placement in shared memory
-      for (u32 ql = tid; ql < L; ql += NT) {
-        const u32 jl = sm.in_j[ql], ci = sm.in_c[ql];
-        const u32 slot = sm.ob[jl] + sm.off[ci][jl] + (ql - sm.first[ci][jl]);
-        sm.out_e[slot] = sm.in_e[ql];
-        sm.out_j[slot] = (uint8_t)jl;
+      // 3. bucket-major placement in shared memory; the same warps walk the
+      //    same pieces and read their elements again (now cached)
+      for (u32 pc = warp; pc < npieces; pc += NW) {
+        u32 ci = 0;
+#pragma unroll
+        for (u32 st = 16; st > 0; st >>= 1)
+          if (ci + st < nc && sm.piece_pre[ci + st] <= pc) ci += st;
+        const u32 a = max(sm.seg_pre[ci], cs);
+        const u32 pa = a + (pc - sm.piece_pre[ci]) * kPiece;
+        const u32 pe = min(min(sm.seg_pre[ci + 1], cs + L), pa + kPiece);
+        for (u32 q = pa + lane; q < pe; q += 32) {
+          const u32 ql = q - cs;
+          const u32 p = sm.seg_start[ci] + (q - sm.seg_pre[ci]);
+          const u32 jl = sm.in_j[ql];
+          const u32 slot = sm.ob[jl] + sm.off[ci][jl] + (ql - sm.first[ci][jl]);
+          sm.out_e[slot] = K::make(dk[p], dv[p]);
+          sm.out_j[slot] = (uint8_t)jl;
+        }
       }
       __syncthreads();
       // 4. coalesced write of every bucket's run
