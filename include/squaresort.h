@@ -190,9 +190,39 @@ uint64_t sq_max_n(sq_dtype dtype);
  * cluster of CTAs merging through distributed shared memory. */
 uint32_t sq_max_leaf(sq_dtype dtype);
 
-/* Default leaf cutoff for `dtype` (0 restores the built-in default). */
+/* Default leaf cutoff for `dtype`; while set it also overrides the cutoff
+ * table below (0 restores the table and the built-in default, the largest
+ * leaf). */
 sq_status sq_set_cutoff(sq_dtype dtype, uint32_t cutoff);
 uint32_t sq_get_cutoff(sq_dtype dtype);
+
+/* Cutoffs by size (written by the autotuner): entry i applies to sorts with
+ * floor(log2 n) == i when non-zero and no cutoff is set with sq_set_cutoff;
+ * count <= 64 entries, the rest are cleared.  The cutoff decides where Algorithm 1
+ * stops recursing (§4.2 sweeps it); results do not depend on it. */
+sq_status sq_set_cutoff_table(sq_dtype dtype, const uint32_t *cutoff_by_log2n, uint32_t count);
+
+/* The cutoff a sort of n keys of `dtype` uses when none is given. */
+uint32_t sq_cutoff_for(sq_dtype dtype, uint64_t n);
+
+/* How the recursion's rounds are launched.  Algorithm 1 runs here breadth
+ * first: every round sorts the pending leaves and takes every ready node
+ * through pivots, counts, SkewTranspose and child creation.
+ *  SQ_LAUNCH_HOST : the host launches each round's kernels with grids sized
+ *                   to the round's work and reads the next round's work
+ *                   counts back (one round trip per round).
+ *  SQ_LAUNCH_GRAPH: all rounds run as one CUDA-graph launch whose device-side
+ *                   loop ends when every instance is sorted; kernels read
+ *                   their work counts on the device.  The graph is built once
+ *                   per thread and device and reused by later calls.
+ *  SQ_LAUNCH_AUTO : (default) the graph for sq_sort_batch and the server,
+ *                   host rounds for sq_sort / sq_sort_ex.
+ * Results do not depend on the mode.  While profiling is on
+ * (sq_set_profiling) rounds are always host-launched, so that every kernel
+ * is timed. */
+typedef enum { SQ_LAUNCH_HOST = 0, SQ_LAUNCH_GRAPH = 1, SQ_LAUNCH_AUTO = 2 } sq_launch_mode;
+sq_status sq_set_launch_mode(sq_launch_mode mode);
+sq_launch_mode sq_get_launch_mode(void);
 
 /* Per-kernel-family counters accumulated by all calls of this process.
  * Families: 0 leaf sort, 1 plan, 2 pivots, 3 count, 4 prefix scan,

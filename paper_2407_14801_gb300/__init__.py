@@ -14,6 +14,7 @@ import os
 from . import build as _build
 
 LIB_PATH = _build.LIB
+TUNING_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.json")
 
 SQ_U32, SQ_U64, SQ_F32 = 0, 1, 2
 DTYPES = {"u32": SQ_U32, "u64": SQ_U64, "f32": SQ_F32}
@@ -81,6 +82,10 @@ def _bind(lib):
         "sq_max_leaf": (u32, [i32]),
         "sq_set_cutoff": (i32, [i32, u32]),
         "sq_get_cutoff": (u32, [i32]),
+        "sq_set_cutoff_table": (i32, [i32, ctypes.POINTER(u32), u32]),
+        "sq_cutoff_for": (u32, [i32, u64]),
+        "sq_set_launch_mode": (i32, [i32]),
+        "sq_get_launch_mode": (i32, []),
         "sq_stats_get": (None, [ctypes.POINTER(Stats)]),
         "sq_stats_reset": (None, []),
         "sq_set_profiling": (None, [i32]),
@@ -99,6 +104,8 @@ def lib():
         if not os.path.exists(LIB_PATH):
             raise ImportError(f"{LIB_PATH} is missing: build it with paper_2407_14801_gb300.build.build()")
         _lib = _bind(ctypes.CDLL(LIB_PATH))
+        if os.environ.get("SQ_NO_TUNING", "") != "1":
+            load_tuning()
     return _lib
 
 
@@ -268,6 +275,55 @@ def set_cutoff(dtype: str, cutoff: int):
 
 def get_cutoff(dtype: str) -> int:
     return int(lib().sq_get_cutoff(DTYPES[dtype]))
+
+
+def set_cutoff_table(dtype: str, table: dict | list):
+    """Cutoffs by size: entry i (a list index or a dict key) applies to sorts
+    of floor(log2 n) == i keys; 0 or absent entries use the default cutoff."""
+    if isinstance(table, dict):
+        arr = [0] * 64
+        for lg, c in table.items():
+            arr[int(lg)] = int(c)
+        while arr and arr[-1] == 0:
+            arr.pop()
+    else:
+        arr = [int(c) for c in table]
+    buf = (ctypes.c_uint32 * max(1, len(arr)))(*arr)
+    _check(lib().sq_set_cutoff_table(DTYPES[dtype], buf, len(arr)))
+
+
+LAUNCH_MODES = {"host": 0, "graph": 1, "auto": 2}
+
+
+def set_launch_mode(mode: str):
+    """'host' (a host round trip per recursion round), 'graph' (all rounds in
+    one CUDA-graph launch) or 'auto' (graph for batches and the server)."""
+    _check(lib().sq_set_launch_mode(LAUNCH_MODES[mode]))
+
+
+def get_launch_mode() -> str:
+    m = int(lib().sq_get_launch_mode())
+    return {v: k for k, v in LAUNCH_MODES.items()}[m]
+
+
+def cutoff_for(dtype: str, n: int) -> int:
+    """The cutoff a sort of n keys uses when the call gives none."""
+    return int(lib().sq_cutoff_for(DTYPES[dtype], n))
+
+
+def load_tuning(path: str | None = None) -> bool:
+    """Applies a cutoff table written by paper_2407_14801_gb300.autotune
+    (default: tuning.json beside this file).  False if there is none."""
+    import json
+
+    path = path or TUNING_PATH
+    if not os.path.exists(path):
+        return False
+    with open(path) as f:
+        doc = json.load(f)
+    for dtype, table in doc.get("cutoff_by_log2n", {}).items():
+        set_cutoff_table(dtype, {int(k): int(v) for k, v in table.items()})
+    return True
 
 
 def stats() -> dict:

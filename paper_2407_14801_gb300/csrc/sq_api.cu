@@ -24,6 +24,8 @@ sq_status fail(sq_status s, const char *fmt, ...) {
 }
 
 std::atomic<uint32_t> g_cutoff[3] = {{0}, {0}, {0}};
+// Per key type and floor(log2 n): the cutoff an autotuner chose (0 = none).
+std::atomic<uint32_t> g_cutoff_table[3][64];
 
 size_t key_bytes(sq_dtype d) { return d == SQ_U64 ? 8 : 4; }
 bool dtype_ok(int d) { return d >= 0 && d <= 2; }
@@ -33,7 +35,46 @@ uint32_t default_cutoff(sq_dtype d) {
   return c ? c : sq::engine_max_leaf(d);
 }
 
+// How recursion rounds are launched (sq_set_launch_mode).
+std::atomic<int> g_launch_mode{SQ_LAUNCH_AUTO};
+
+int graph_for(bool many) {
+  const int m = g_launch_mode.load();
+  return m == SQ_LAUNCH_GRAPH || (m == SQ_LAUNCH_AUTO && many) ? 1 : 0;
+}
+
+// A cutoff set with sq_set_cutoff wins; else the tuned table's entry for
+// floor(log2 n); else the largest leaf.
+uint32_t cutoff_for(sq_dtype d, uint64_t n) {
+  if (g_cutoff[d].load()) return g_cutoff[d].load();
+  if (n) {
+    const int lg = 63 - __builtin_clzll(n);
+    const uint32_t t = g_cutoff_table[d][lg].load();
+    if (t) return t;
+  }
+  return default_cutoff(d);
+}
+
+// Scratch comes from the device's default stream-ordered pool.  By default
+// that pool hands freed memory back to the driver at every synchronisation,
+// so each call would map its scratch afresh; keeping it cached (once per
+// device, for this process) makes repeated sorts allocation-cheap.
+void keep_pool_cached() {
+  static std::atomic<uint64_t> done_mask{0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  if (done_mask.load() & (1ull << dev)) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
+  done_mask.fetch_or(1ull << dev);
+}
+
 int run_engine(sq_dtype d, const sq::RunSpec &spec, cudaStream_t st, char *err, size_t len) {
+  if (!spec.dev_alloc) keep_pool_cached();
   switch (d) {
     case SQ_U32: return sq::engine_run_u32(spec, st, err, len);
     case SQ_U64: return sq::engine_run_u64(spec, st, err, len);
@@ -66,8 +107,9 @@ struct DevBuf {
 // Sorts one instance whose buffers are device memory.
 sq_status sort_device(void *keys, uint32_t *vals, uint64_t n, sq_dtype dtype, uint64_t seed, cudaStream_t st,
                       const sq_sort_opts *opts) {
-  const uint32_t cutoff = (opts && opts->cutoff) ? opts->cutoff : default_cutoff(dtype);
+  const uint32_t cutoff = (opts && opts->cutoff) ? opts->cutoff : cutoff_for(dtype, n);
   const size_t w = key_bytes(dtype);
+  keep_pool_cached();
   DevBuf scratch, iota;
   scratch.st = iota.st = st;
   cudaError_t e = cudaMallocAsync(&scratch.p, std::max<size_t>(n, 1) * (w + 4) + 256, st);
@@ -80,7 +122,7 @@ sq_status sort_device(void *keys, uint32_t *vals, uint64_t n, sq_dtype dtype, ui
     v = (uint32_t *)iota.p;
     k_iota<<<std::max<uint64_t>(1, std::min<uint64_t>((n + 255) / 256, 4096)), 256, 0, st>>>(v, n);
   }
-  sq::InstSpec is;
+  sq::InstSpec is{};
   is.keys = keys;
   is.vals = v;
   is.dkeys = scratch.p;
@@ -92,6 +134,7 @@ sq_status sort_device(void *keys, uint32_t *vals, uint64_t n, sq_dtype dtype, ui
   spec.inst = &is;
   spec.ninst = 1;
   spec.cutoff = cutoff;
+  spec.graph = graph_for(false);
   std::vector<sq::TraceOut> tr;
   if (opts && opts->trace && opts->trace_cap) {
     tr.resize(opts->trace_cap);
@@ -146,6 +189,28 @@ sq_status sq_set_cutoff(sq_dtype dtype, uint32_t cutoff) {
 }
 
 uint32_t sq_get_cutoff(sq_dtype dtype) { return dtype_ok(dtype) ? default_cutoff(dtype) : 0; }
+
+sq_status sq_set_cutoff_table(sq_dtype dtype, const uint32_t *cutoff_by_log2n, uint32_t count) {
+  if (!dtype_ok(dtype)) return fail(SQ_ERR_INVALID, "bad dtype %d", (int)dtype);
+  if (count > 64 || (count && !cutoff_by_log2n)) return fail(SQ_ERR_INVALID, "table of %u entries", count);
+  for (uint32_t i = 0; i < count; i++)
+    if (cutoff_by_log2n[i] != 0 && (cutoff_by_log2n[i] < 2 || cutoff_by_log2n[i] > sq::engine_max_leaf(dtype)))
+      return fail(SQ_ERR_INVALID, "table entry %u: cutoff %u outside [2, %u]", i, cutoff_by_log2n[i],
+                  sq::engine_max_leaf(dtype));
+  for (uint32_t i = 0; i < 64; i++) g_cutoff_table[dtype][i].store(i < count ? cutoff_by_log2n[i] : 0);
+  return SQ_OK;
+}
+
+uint32_t sq_cutoff_for(sq_dtype dtype, uint64_t n) { return dtype_ok(dtype) ? cutoff_for(dtype, n) : 0; }
+
+sq_status sq_set_launch_mode(sq_launch_mode mode) {
+  if (mode != SQ_LAUNCH_HOST && mode != SQ_LAUNCH_GRAPH && mode != SQ_LAUNCH_AUTO)
+    return fail(SQ_ERR_INVALID, "bad launch mode %d", (int)mode);
+  g_launch_mode.store(mode);
+  return SQ_OK;
+}
+
+sq_launch_mode sq_get_launch_mode(void) { return (sq_launch_mode)g_launch_mode.load(); }
 
 sq_status sq_sort_ex(void *keys, uint32_t *vals, uint64_t n, sq_dtype dtype, uint64_t seed, sq_stream_t stream,
                      const sq_sort_opts *opts) {
@@ -213,7 +278,7 @@ sq_status sq_skew_transpose(const sq_skew_buf *buf, uint64_t rows, uint64_t cols
   if (!buf->bucket_start_out || (n && (!buf->keys_in || !buf->vals_in || !buf->keys_out || !buf->vals_out)) ||
       (k > 1 && (!buf->pivot_keys || !buf->pivot_vals)))
     return fail(SQ_ERR_INVALID, "null buffer");
-  sq::InstSpec is;
+  sq::InstSpec is{};
   is.keys = buf->keys_out;
   is.vals = buf->vals_out;
   is.dkeys = const_cast<void *>(buf->keys_in);
@@ -276,6 +341,7 @@ sq_status sq_sort_batch(const sq_sort_desc *descs, uint32_t count, sq_stream_t s
     }
     DevBuf slab;
     slab.st = st;
+    keep_pool_cached();
     cudaError_t e = cudaMallocAsync(&slab.p, std::max<size_t>(off, 256), st);
     if (e != cudaSuccess) return fail(SQ_ERR_NOMEM, "batch scratch: %s", cudaGetErrorString(e));
     std::vector<sq::InstSpec> is(ids.size());
@@ -292,12 +358,14 @@ sq_status sq_sort_batch(const sq_sort_desc *descs, uint32_t count, sq_stream_t s
       is[q].dvals = (uint32_t *)((char *)slab.p + voff[q]);
       is[q].n = ds.n;
       is[q].seed = ds.seed;
+      is[q].cutoff = cutoff_for((sq_dtype)d, ds.n);
     }
     sq::RunSpec spec;
     memset(&spec, 0, sizeof(spec));
     spec.inst = is.data();
     spec.ninst = (uint32_t)is.size();
     spec.cutoff = default_cutoff((sq_dtype)d);
+    spec.graph = graph_for(true);
     char err[400] = {0};
     const int rc = run_engine((sq_dtype)d, spec, st, err, sizeof(err));
     if (rc) return fail((sq_status)rc, "batch: %s", err);

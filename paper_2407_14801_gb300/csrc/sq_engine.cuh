@@ -90,16 +90,44 @@ struct Engine {
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   }
 
+  // Grid of a launch whose item count the kernel reads on the device: enough
+  // CTAs (or clusters) to fill every SM; the kernel strides over its list.
+  template <class Kern>
+  static u32 fill_grid(Kern kern, int threads, size_t smem, int nsm) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem) != cudaSuccess || occ < 1) occ = 1;
+    return (u32)occ * (u32)nsm;
+  }
+  template <class Kern>
+  static u32 fill_clusters(Kern kern, int threads, size_t smem, int G, int nsm) {
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)(G * std::max(1, nsm / G)), 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = G;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg) != cudaSuccess || ncl < 1) ncl = std::max(1, nsm / G);
+    return (u32)ncl * (u32)G;
+  }
+
   template <int T, int R, bool WARP>
-  static cudaError_t launch_leaf(Launcher &L, const Ctx &c, int cls, u32 count) {
+  static cudaError_t launch_leaf(Launcher &L, const Ctx *cp, int cls, u32 count, int nsm) {
     typedef Sorter<K, T, R, WARP> S;
     const size_t smem = (size_t)(WARP ? 8 : 1) * S::SMEM * sizeof(E);
     auto kern = k_leaf<DT, T, R, WARP>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    const u32 grid = WARP ? (count + 7) / 8 : count;
+    const int threads = WARP ? 256 : T;
+    const u32 grid = count == kDev ? fill_grid(kern, threads, smem, nsm) : (WARP ? (count + 7) / 8 : count);
     L.begin(KF_LEAF);
-    kern<<<grid, WARP ? 256 : T, smem, L.st>>>(c, cls, count);
+    kern<<<grid, threads, smem, L.st>>>(cp, cls, count);
     L.end();
     return cudaGetLastError();
   }
@@ -125,54 +153,57 @@ struct Engine {
   }
 
   template <int T, int R, int G>
-  static cudaError_t launch_leaf_radix(Launcher &L, const Ctx &c, int cls, u32 count) {
+  static cudaError_t launch_leaf_radix(Launcher &L, const Ctx *cp, int cls, u32 count, int nsm) {
     const size_t smem = RadixSorter<K, T, R, G>::kSmem;
     auto kern = k_leaf_radix<DT, T, R, G>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
     L.begin(KF_LEAF);
     if (G == 1) {
-      kern<<<count, T, smem, L.st>>>(c, cls, count);
+      const u32 grid = count == kDev ? fill_grid(kern, T, smem, nsm) : count;
+      kern<<<grid, T, smem, L.st>>>(cp, cls, count);
       e = cudaGetLastError();
     } else {
-      e = launch_cluster(kern, dim3(count * G, 1, 1), T, smem, G, L.st, c, cls, count);
+      const u32 grid = count == kDev ? fill_clusters(kern, T, smem, G, nsm) : count * G;
+      e = launch_cluster(kern, dim3(grid, 1, 1), T, smem, G, L.st, cp, cls, count);
     }
     L.end();
     return e;
   }
 
   template <int T, int R, int G>
-  static cudaError_t launch_leaf_cluster(Launcher &L, const Ctx &c, int cls, u32 count) {
+  static cudaError_t launch_leaf_cluster(Launcher &L, const Ctx *cp, int cls, u32 count, int nsm) {
     const size_t smem = sizeof(E) * (size_t)Sorter<K, T, R, false>::SMEM;
     auto kern = k_leaf_cluster<DT, T, R, G>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
+    const u32 grid = count == kDev ? fill_clusters(kern, T, smem, G, nsm) : count * G;
     L.begin(KF_LEAF);
-    e = launch_cluster(kern, dim3(count * G, 1, 1), T, smem, G, L.st, c, cls, count);
+    e = launch_cluster(kern, dim3(grid, 1, 1), T, smem, G, L.st, cp, cls, count);
     L.end();
     return e;
   }
 
-  static cudaError_t launch_leaf_class(Launcher &L, const Ctx &c, int cls, u32 count) {
+  static cudaError_t launch_leaf_class(Launcher &L, const Ctx *cp, int cls, u32 count, int nsm) {
     switch (cls) {
-      case 0: return launch_leaf<32, 2, true>(L, c, 0, count);
-      case 1: return launch_leaf<32, 16, true>(L, c, 1, count);
-      case 2: return launch_leaf<128, 16, false>(L, c, 2, count);
-      case 3: return launch_leaf_radix<512, 16, 1>(L, c, 3, count);
+      case 0: return launch_leaf<32, 2, true>(L, cp, 0, count, nsm);
+      case 1: return launch_leaf<32, 16, true>(L, cp, 1, count, nsm);
+      case 2: return launch_leaf<128, 16, false>(L, cp, 2, count, nsm);
+      case 3: return launch_leaf_radix<512, 16, 1>(L, cp, 3, count, nsm);
       case 4:
-        if constexpr (sizeof(E) == 8) return launch_leaf<1024, 16, false>(L, c, 4, count);
-        else return launch_leaf_cluster<512, 16, 2>(L, c, 4, count);
+        if constexpr (sizeof(E) == 8) return launch_leaf<1024, 16, false>(L, cp, 4, count, nsm);
+        else return launch_leaf_cluster<512, 16, 2>(L, cp, 4, count, nsm);
       case 5:
-        if constexpr (sizeof(E) == 8) return launch_leaf_cluster<1024, 16, 2>(L, c, 5, count);
-        else return launch_leaf_cluster<512, 16, 4>(L, c, 5, count);
+        if constexpr (sizeof(E) == 8) return launch_leaf_cluster<1024, 16, 2>(L, cp, 5, count, nsm);
+        else return launch_leaf_cluster<512, 16, 4>(L, cp, 5, count, nsm);
       default:
-        if constexpr (sizeof(E) == 8) return launch_leaf_cluster<1024, 16, 4>(L, c, 6, count);
-        else return launch_leaf_cluster<512, 16, 8>(L, c, 6, count);
+        if constexpr (sizeof(E) == 8) return launch_leaf_cluster<1024, 16, 4>(L, cp, 6, count, nsm);
+        else return launch_leaf_cluster<512, 16, 8>(L, cp, 6, count, nsm);
     }
   }
 
   // The (key, val) merge sort of leaves whose radix check failed this round.
-  static cudaError_t launch_fixup(Launcher &L, const Ctx &c, int nsm) {
+  static cudaError_t launch_fixup(Launcher &L, const Ctx *cp, int nsm) {
     constexpr bool wide = sizeof(E) == 8;
     constexpr int T = wide ? 1024 : 512, R = 16, G = wide ? 4 : 8;
     const size_t smem = sizeof(E) * (size_t)Sorter<K, T, R, false>::SMEM;
@@ -180,34 +211,263 @@ struct Engine {
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
     L.begin(KF_AUX);
-    e = launch_cluster(kern, dim3(std::max(1, nsm / G) * G, 1, 1), T, smem, G, L.st, c);
+    e = launch_cluster(kern, dim3(std::max(1, nsm / G) * G, 1, 1), T, smem, G, L.st, cp);
     L.end();
     return e;
   }
 
   template <int T, int R, bool WARP>
-  static cudaError_t launch_pivots(Launcher &L, const Ctx &c, u32 ready, u32 pmin, u32 pmax) {
+  static cudaError_t launch_pivots(Launcher &L, const Ctx *cp, u32 ready, u32 pmin, u32 pmax, int nsm) {
     typedef Sorter<K, T, R, WARP> S;
     const size_t smem = (size_t)(WARP ? 8 : 1) * S::SMEM * sizeof(E);
     auto kern = k_pivots<DT, T, R, WARP>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    const u32 grid = WARP ? (ready + 7) / 8 : ready;
+    const int threads = WARP ? 256 : T;
+    const u32 grid = ready == kDev ? fill_grid(kern, threads, smem, nsm) : (WARP ? (ready + 7) / 8 : ready);
     L.begin(KF_PIVOTS);
-    kern<<<grid, WARP ? 256 : T, smem, L.st>>>(c, ready, pmin, pmax);
+    kern<<<grid, threads, smem, L.st>>>(cp, ready, pmin, pmax);
     L.end();
     return cudaGetLastError();
   }
 
-  static cudaError_t launch_all_pivots(Launcher &L, const Ctx &c, u32 ready, u32 max_k) {
+  static cudaError_t launch_all_pivots(Launcher &L, const Ctx *cp, u32 ready, u32 max_k, int nsm) {
     cudaError_t e = cudaSuccess;
     const u32 maxp = max_k ? max_k - 1 : 0;
-    e = launch_pivots<32, 16, true>(L, c, ready, 0, 512);
-    if (e == cudaSuccess && maxp > 512) e = launch_pivots<128, 16, false>(L, c, ready, 512, 2048);
-    if (e == cudaSuccess && maxp > 2048) e = launch_pivots<512, 16, false>(L, c, ready, 2048, 8192);
+    e = launch_pivots<32, 16, true>(L, cp, ready, 0, 512, nsm);
+    if (e == cudaSuccess && maxp > 512) e = launch_pivots<128, 16, false>(L, cp, ready, 512, 2048, nsm);
+    if (e == cudaSuccess && maxp > 2048) e = launch_pivots<512, 16, false>(L, cp, ready, 2048, 8192, nsm);
     if constexpr (LeafCfg<DT>::max_pivots > 8192)
-      if (e == cudaSuccess && maxp > 8192) e = launch_pivots<1024, 16, false>(L, c, ready, 8192, 16384);
+      if (e == cudaSuccess && maxp > 8192) e = launch_pivots<1024, 16, false>(L, cp, ready, 8192, 16384, nsm);
     return e;
+  }
+
+  // ---- one round ----------------------------------------------------------
+  // Leaves (simple_sort), then for the ready nodes the plan, pivots, counts,
+  // bucket starts, SkewTranspose and bucket children, then the column
+  // children of new nodes.  hc: the round's counts when the host drives the
+  // rounds (launches sized to them, empty steps skipped); null for a graph
+  // round, whose kernels read the counts on the device.
+  struct RoundArgs {
+    int nsm;
+    int skew_only;
+    const void *piv_keys;
+    const u32 *piv_vals;
+    u64 *bucket_start;
+    u64 k;
+    double skew_elems;  // skew_only: elements moved
+  };
+
+  static cudaError_t issue_round(Launcher &L, const Ctx *cp, const Counters *hc, const RoundArgs &A) {
+    const cudaStream_t st = L.st;
+    const int nsm = A.nsm;
+    const int grid_count = nsm * 2, grid_scan = nsm * 8, grid_skew = nsm * 5, grid_expand = nsm * 4;
+    cudaError_t e;
+#define SQ_TRY(x)                      \
+  do {                                 \
+    if ((e = (x)) != cudaSuccess) return e; \
+  } while (0)
+    L.begin(KF_AUX);
+    k_round_begin<<<1, 64, 0, st>>>(cp);
+    L.end();
+    SQ_TRY(cudaGetLastError());
+    bool radix_leaves = false;
+    for (int cl = 0; cl < NCLASS; cl++) {
+      const u32 n = hc ? hc->leaves[cl] : kDev;
+      if (!n) continue;
+      if (hc) L.local.bytes[KF_LEAF] += 2.0 * (KEY_BYTES + 4) * (double)hc->leaf_elems[cl];
+      SQ_TRY(launch_leaf_class(L, cp, cl, n, nsm));
+      radix_leaves |= cl == 3;
+    }
+    if (radix_leaves) SQ_TRY(launch_fixup(L, cp, nsm));
+    const u32 ready = hc ? hc->ready : kDev;
+    if (ready) {
+      const double re = A.skew_only ? A.skew_elems : (hc ? (double)hc->ready_elems : 0.0);
+      if (hc) L.local.nodes += A.skew_only ? 0 : ready;
+      L.begin(KF_PLAN);
+      k_plan<<<1, 1024, 0, st>>>(cp, ready, K::key_words);
+      L.end();
+      SQ_TRY(cudaGetLastError());
+      const u32 kmax = hc ? std::max<u32>(hc->max_ready_k, 2) : max_pivots() + 1;
+      if (A.skew_only) {
+        L.begin(KF_AUX);
+        k_put_pivots<DT><<<((u32)A.k + 255) / 256, 256, 0, st>>>(cp, (const typename K::key_t *)A.piv_keys,
+                                                                  A.piv_vals);
+        L.end();
+        SQ_TRY(cudaGetLastError());
+      } else {
+        SQ_TRY(launch_all_pivots(L, cp, ready, kmax, nsm));
+      }
+      const size_t smem_count = (size_t)(kmax - 1) * sizeof(E) + (size_t)kmax * 4;
+      SQ_TRY(set_smem(k_count<DT>, smem_count));
+      L.begin(KF_COUNT);
+      k_count<DT><<<grid_count, 1024, smem_count, st>>>(cp, ready, kmax);
+      L.end();
+      L.local.bytes[KF_COUNT] += (KEY_BYTES + 4) * re;
+      SQ_TRY(cudaGetLastError());
+      L.begin(KF_SCAN);
+      k_scan<<<grid_scan, 256, 0, st>>>(cp, ready, K::key_words);
+      L.end();
+      SQ_TRY(cudaGetLastError());
+      L.begin(KF_BSTART);
+      k_bstart<<<hc ? ready : (u32)nsm * 2, 1024, 0, st>>>(cp, ready, K::key_words);
+      L.end();
+      SQ_TRY(cudaGetLastError());
+      const size_t smem_skew = sizeof(SkewSmem<DT, SKEW_CAP>);
+      SQ_TRY(set_smem(k_skew<DT, SKEW_CAP>, smem_skew));
+      L.begin(KF_SKEW);
+      k_skew<DT, SKEW_CAP><<<grid_skew, 256, smem_skew, st>>>(cp, ready);
+      L.end();
+      L.local.bytes[KF_SKEW] += 2.0 * (KEY_BYTES + 4) * re;
+      SQ_TRY(cudaGetLastError());
+      if (A.skew_only) {
+        L.begin(KF_AUX);
+        k_get_bstart<DT><<<((u32)A.k + 256) / 256, 256, 0, st>>>(cp, A.bucket_start);
+        L.end();
+        SQ_TRY(cudaGetLastError());
+      } else {
+        L.begin(KF_EXPAND);
+        k_expand_buckets<DT><<<grid_expand, 256, 0, st>>>(cp, ready);
+        L.end();
+        SQ_TRY(cudaGetLastError());
+      }
+    }
+    if (!A.skew_only && (!hc || ready || hc->fresh)) {
+      L.begin(KF_EXPAND);
+      k_expand_cols<DT><<<grid_expand, 256, 0, st>>>(cp);
+      L.end();
+      SQ_TRY(cudaGetLastError());
+    }
+#undef SQ_TRY
+    return cudaSuccess;
+  }
+
+  // Pinned host memory (512 bytes) for the round read-backs, one buffer per
+  // thread, allocated on first use and kept: pinning per call costs more
+  // than a whole small sort.
+  static cudaError_t pinned_readback(void **out) {
+    struct Pinned {
+      void *p = nullptr;
+      ~Pinned() {
+        if (p) cudaFreeHost(p);
+      }
+    };
+    static thread_local Pinned buf;
+    if (!buf.p) {
+      const cudaError_t e = cudaMallocHost(&buf.p, 512);
+      if (e != cudaSuccess) {
+        buf.p = nullptr;
+        return e;
+      }
+    }
+    *out = buf.p;
+    return cudaSuccess;
+  }
+
+  // ---- CUDA-graph rounds ----------------------------------------------------
+  // The recursion as one graph launch: a device-side while loop whose body is
+  // two rounds (the even and the odd parity of the double-buffered lists), the
+  // second under a condition, each ended by k_round_end, which sets the
+  // conditions.  Every launch reads its context from ctx[0] (the first round
+  // of the body) or ctx[1] and its item counts from the device, so one
+  // instantiated graph serves every run of this key type on this thread.
+  struct GraphSlot {
+    int dev = -1, nsm = 0;
+    Ctx *ctx = nullptr;  // device, 2 contexts
+    GraphStats *gs = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    EngineStats per_round{};  // launches of one round, by family
+    void reset() {
+      if (exec) cudaGraphExecDestroy(exec);
+      if (graph) cudaGraphDestroy(graph);
+      if (cap) cudaStreamDestroy(cap);
+      if (ctx) cudaFree(ctx);
+      exec = nullptr;
+      graph = nullptr;
+      cap = nullptr;
+      ctx = nullptr;
+      gs = nullptr;
+      dev = -1;
+    }
+    ~GraphSlot() { reset(); }
+  };
+  static GraphSlot &graph_slot() {
+    static thread_local GraphSlot s;
+    return s;
+  }
+
+  static constexpr unsigned long long kMaxRounds = 4096;  // far above any recursion depth
+
+  // Builds (once per thread, device and instance count) the graph of rounds.
+  static int graph_prepare(GraphSlot &G, int dev, int nsm, char *err, size_t errlen) {
+    if (G.exec && G.dev == dev) return 0;
+    G.reset();
+    SQ_CU(cudaMalloc((void **)&G.ctx, 2 * sizeof(Ctx) + sizeof(GraphStats)));
+    G.gs = reinterpret_cast<GraphStats *>(G.ctx + 2);
+    SQ_CU(cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking));
+    SQ_CU(cudaGraphCreate(&G.graph, 0));
+    cudaGraphConditionalHandle loop, second;
+    SQ_CU(cudaGraphConditionalHandleCreate(&loop, G.graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams wp = {};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = loop;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    SQ_CU(cudaGraphAddNode(&wnode, G.graph, nullptr, nullptr, 0, &wp));
+    cudaGraph_t body = wp.conditional.phGraph_out[0];
+    SQ_CU(cudaGraphConditionalHandleCreate(&second, body, 0, 0));
+    Launcher L;
+    L.st = G.cap;
+    L.prof = false;
+    RoundArgs A;
+    memset(&A, 0, sizeof(A));
+    A.nsm = nsm;
+    // first round of the body, then the conditional second round
+    SQ_CU(cudaStreamBeginCaptureToGraph(G.cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    cudaError_t ce = issue_round(L, G.ctx, nullptr, A);
+    if (ce == cudaSuccess) {
+      k_round_end<<<1, 1, 0, G.cap>>>(G.ctx, loop, second, 1, G.gs, kMaxRounds);
+      ce = cudaGetLastError();
+    }
+    // the captured round's last node(s): the conditional second round follows them
+    std::vector<cudaGraphNode_t> tail;
+    if (ce == cudaSuccess) {
+      cudaStreamCaptureStatus cs;
+      const cudaGraphNode_t *deps = nullptr;
+      size_t nl = 0;
+      ce = cudaStreamGetCaptureInfo(G.cap, &cs, nullptr, nullptr, &deps, nullptr, &nl);
+      if (ce == cudaSuccess) tail.assign(deps, deps + nl);
+    }
+    cudaGraph_t got = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(G.cap, &got);
+    SQ_CU(ce);
+    SQ_CU(ee);
+    const size_t nl = tail.size();
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = second;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t inode;
+    SQ_CU(cudaGraphAddNode(&inode, body, tail.data(), nullptr, nl, &ip));
+    cudaGraph_t body2 = ip.conditional.phGraph_out[0];
+    SQ_CU(cudaStreamBeginCaptureToGraph(G.cap, body2, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    ce = issue_round(L, G.ctx + 1, nullptr, A);
+    if (ce == cudaSuccess) {
+      k_round_end<<<1, 1, 0, G.cap>>>(G.ctx + 1, loop, second, 0, G.gs, kMaxRounds);
+      ce = cudaGetLastError();
+    }
+    ee = cudaStreamEndCapture(G.cap, &got);
+    SQ_CU(ce);
+    SQ_CU(ee);
+    SQ_CU(cudaGraphInstantiate(&G.exec, G.graph, 0));
+    for (int f = 0; f < KF_COUNT_FAMILIES; f++) G.per_round.launches[f] = L.local.launches[f] / 2;
+    G.dev = dev;
+    G.nsm = nsm;
+    return 0;
   }
 
   // ---- scratch plan: list capacities (proven bounds) and slab layout ------
@@ -215,7 +475,7 @@ struct Engine {
     u32 leaf_cap[kLeafClasses];
     u64 ready_cap, fresh_cap, node_cap, meta_cap;
     size_t o_inst, o_leaves[2][kLeafClasses], o_ready[2], o_fresh[2], o_cnt, o_status, o_meta, o_done, o_trace,
-        o_wbase, o_fix;
+        o_wbase, o_fix, o_ctx;
     u64 fix_cap;
     size_t slab_bytes;
   };
@@ -224,14 +484,17 @@ struct Engine {
   // or buckets of nodes with n > cutoff (at most 2*ceil(sqrt n) each), so a
   // round makes at most 2*(N/floor(sqrt c) + N/c) of them; ready nodes
   // (n > c, disjoint) number at most N/(c+1), new nodes twice that.
-  static Plan make_plan(u64 total_n, u32 ninst, u32 cutoff, u32 trace_cap, int skew_only, u32 k, u32 cols) {
+  // cutoff: the smallest cutoff of the run's instances (bounds the counts of
+  // leaves and nodes); cutoff_max: the largest (bounds the leaf classes).
+  static Plan make_plan(u64 total_n, u32 ninst, u32 cutoff, u32 cutoff_max, u32 trace_cap, int skew_only, u32 k,
+                        u32 cols) {
     Plan P;
     const double sc = std::floor(std::sqrt((double)cutoff));
     const u64 leaf_bound = (u64)(2.0 * ((double)total_n / sc + (double)total_n / cutoff)) + 2ull * ninst + 64;
     for (int c = 0; c < kLeafClasses; c++) {
       const u64 lo = c == 0 ? 1 : (u64)class_cap(c - 1) + 1;
       u64 cap = std::min<u64>(leaf_bound, total_n / lo + ninst + 64);
-      if (lo > cutoff || c >= NCLASS) cap = 0;  // no leaf of this class can exist
+      if (lo > cutoff_max || c >= NCLASS) cap = 0;  // no leaf of this class can exist
       P.leaf_cap[c] = (u32)std::min<u64>(cap, 0xffffffffull);
     }
     P.ready_cap = total_n / (cutoff + 1) + ninst + 64;
@@ -272,25 +535,37 @@ struct Engine {
     P.fix_cap = 0;
     for (int c = 3; c < kLeafClasses; c++) P.fix_cap += P.leaf_cap[c];
     P.o_fix = carve(sizeof(Leaf) * (size_t)P.fix_cap);
+    P.o_ctx = carve(2 * sizeof(Ctx));
     P.slab_bytes = off;
     return P;
   }
 
   static u64 skew_scratch_bytes(u64 n, u32 cols, u32 k) {
-    const Plan P = make_plan(n, 1, 2, 0, 1, k, cols);
+    const Plan P = make_plan(n, 1, 2, 2, 0, 1, k, cols);
     return ((P.slab_bytes + 255) & ~(u64)255) + ((sizeof(Node) + 255) & ~(u64)255);
   }
 
-  static u64 scratch_bytes(u64 total_n, u32 ninst, u32 cutoff) {
-    const Plan P = make_plan(total_n, ninst, cutoff, 0, 0, 0, 0);
+  static u64 scratch_bytes(u64 total_n, u32 ninst, u32 cutoff, u32 cutoff_max) {
+    const Plan P = make_plan(total_n, ninst, cutoff, std::max(cutoff, cutoff_max), 0, 0, 0, 0);
     return P.slab_bytes + sizeof(Node) * P.node_cap + 4096;
   }
 
   // ---- one run ------------------------------------------------------------
   static int run(const RunSpec &spec, cudaStream_t st, char *err, size_t errlen) {
     const u32 ninst = spec.ninst;
-    const u32 cutoff = spec.cutoff;
-    if (cutoff < 2 || cutoff > max_leaf()) {
+    auto cutoff_of = [&](u32 i) { return spec.inst[i].cutoff ? spec.inst[i].cutoff : spec.cutoff; };
+    u32 cutoff = ninst ? 0xffffffffu : spec.cutoff;  // the smallest cutoff bounds the work lists
+    u32 cutoff_max = spec.cutoff;
+    for (u32 i = 0; i < ninst; i++) {
+      const u32 ci = cutoff_of(i);
+      if (ci < 2 || ci > max_leaf()) {
+        snprintf(err, errlen, "cutoff %u outside [2, %u]", ci, max_leaf());
+        return 1;
+      }
+      cutoff = std::min(cutoff, ci);
+      cutoff_max = std::max(cutoff_max, ci);
+    }
+    if (cutoff < 2) {
       snprintf(err, errlen, "cutoff %u outside [2, %u]", cutoff, max_leaf());
       return 1;
     }
@@ -310,7 +585,7 @@ struct Engine {
                (unsigned long long)max_n, (unsigned long long)lim);
       return 1;
     }
-    const Plan P = make_plan(total_n, ninst, cutoff, spec.trace_cap, spec.skew_only, (u32)spec.k, (u32)spec.cols);
+    const Plan P = make_plan(total_n, ninst, cutoff, cutoff_max, spec.trace_cap, spec.skew_only, (u32)spec.k, (u32)spec.cols);
     u32 leaf_cap[kLeafClasses];
     for (int cl = 0; cl < kLeafClasses; cl++) leaf_cap[cl] = P.leaf_cap[cl];
     const u64 ready_cap = P.ready_cap, fresh_cap = P.fresh_cap, meta_cap = P.meta_cap;
@@ -370,7 +645,24 @@ struct Engine {
     c.cutoff = cutoff;
     for (int cl = 0; cl < kLeafClasses; cl++) c.class_cap[cl] = class_cap(cl);
     c.recurse = spec.skew_only ? 0 : 1;
+    c.ninst = ninst;
     Counters *cnt = (Counters *)(slab + o_cnt);
+    // the contexts of the two list parities (round r reads lists r & 1)
+    Ctx hctx[2];
+    for (int q = 0; q < 2; q++) {
+      hctx[q] = c;
+      for (int cl = 0; cl < kLeafClasses; cl++) {
+        hctx[q].leaves_cur[cl] = (Leaf *)(slab + o_leaves[q][cl]);
+        hctx[q].leaves_nxt[cl] = (Leaf *)(slab + o_leaves[q ^ 1][cl]);
+      }
+      hctx[q].ready_cur = (u32 *)(slab + o_ready[q]);
+      hctx[q].ready_nxt = (u32 *)(slab + o_ready[q ^ 1]);
+      hctx[q].fresh_cur = (u32 *)(slab + o_fresh[q]);
+      hctx[q].fresh_nxt = (u32 *)(slab + o_fresh[q ^ 1]);
+      hctx[q].cnt_cur = cnt + q;
+      hctx[q].cnt_nxt = cnt + (q ^ 1);
+    }
+    Ctx *cdev = (Ctx *)(slab + P.o_ctx);
 
     // ---- seed the roots (host-built records)
     std::vector<Inst> hinst(ninst);
@@ -388,12 +680,14 @@ struct Engine {
       hinst[i].dkeys = is.dkeys;
       hinst[i].dvals = is.dvals;
       hinst[i].n = is.n;
+      hinst[i].cutoff = cutoff_of(i);
+      hinst[i].pad = 0;
       if (spec.skew_only) continue;
       if (is.n == 0) {
         hs.done++;
         continue;
       }
-      if (is.n <= cutoff) {
+      if (is.n <= hinst[i].cutoff) {
         int cl = 0;
         while (cl < NCLASS - 1 && is.n > class_cap(cl)) ++cl;
         Leaf L;
@@ -417,7 +711,7 @@ struct Engine {
         nd.kind = KIND_ROOT;
         nd.out = 0;
         const u32 id = (u32)hnodes.size();
-        if (m <= cutoff && m >= kHostExpandCols) {
+        if (m <= hinst[i].cutoff && m >= kHostExpandCols) {
           // a large root whose columns are leaves: spawn them here rather than
           // in one CTA of k_expand_cols
           const u32 ncol = (u32)((is.n + m - 1) / m);
@@ -475,139 +769,118 @@ struct Engine {
     Launcher L;
     L.st = st;
     L.prof = stats_box().profiling.load() != 0;
-    struct Readback {
-      Counters cnt;
-      Status status;
-    };
-    static_assert(sizeof(Readback) <= 512, "read-back buffer contract");
-    Readback *hrb = reinterpret_cast<Readback *>(spec.host_readback);
-    if (!hrb) SQ_CU(cudaMallocHost((void **)&hrb, sizeof(Readback)));
-    struct FreeHost {
-      Readback *p;
-      ~FreeHost() {
-        if (p) cudaFreeHost(p);
-      }
-    } fh{spec.host_readback ? nullptr : hrb};
-    Counters cur_cnt = hc[0];
+    SQ_CU(cudaMemcpyAsync(cdev, hctx, sizeof(hctx), cudaMemcpyHostToDevice, st));
+    RoundArgs A;
+    memset(&A, 0, sizeof(A));
+    A.nsm = nsm;
+    A.skew_only = spec.skew_only;
+    A.piv_keys = spec.piv_keys;
+    A.piv_vals = spec.piv_vals;
+    A.bucket_start = (u64 *)spec.bucket_start;
+    A.k = spec.k;
+    A.skew_elems = spec.skew_only ? (double)spec.inst[0].n : 0.0;
     u32 done = hs.done;
     int rc = 0;
     u64 rounds = 0;
-    const int grid_count = nsm * 2, grid_scan = nsm * 8, grid_skew = nsm * 5, grid_expand = nsm * 4;
-    for (u32 r = 0;; r++) {
-      const int cur = r & 1, nxt = cur ^ 1;
-      if (!spec.skew_only && done >= ninst) break;
-      if (spec.skew_only && r == 1) break;
-      if (r > 100000) {
-        snprintf(err, errlen, "recursion did not finish");
-        rc = 8;
-        break;
-      }
-      rounds++;
-      for (int cl = 0; cl < kLeafClasses; cl++) {
-        c.leaves_cur[cl] = (Leaf *)(slab + o_leaves[cur][cl]);
-        c.leaves_nxt[cl] = (Leaf *)(slab + o_leaves[nxt][cl]);
-      }
-      c.ready_cur = (u32 *)(slab + o_ready[cur]);
-      c.ready_nxt = (u32 *)(slab + o_ready[nxt]);
-      c.fresh_cur = (u32 *)(slab + o_fresh[cur]);
-      c.fresh_nxt = (u32 *)(slab + o_fresh[nxt]);
-      c.cnt_cur = cnt + cur;
-      c.cnt_nxt = cnt + nxt;
-      SQ_CU(cudaMemsetAsync(cnt + nxt, 0, sizeof(Counters), st));
-      SQ_CU(cudaMemsetAsync(&c.status->cur_count, 0, 7 * sizeof(u32), st));
-      // leaves (simple_sort)
-      bool radix_leaves = false;
-      for (int cl = 0; cl < NCLASS; cl++) {
-        if (!cur_cnt.leaves[cl]) continue;
-        L.local.bytes[KF_LEAF] += 2.0 * (KEY_BYTES + 4) * (double)cur_cnt.leaf_elems[cl];
-        SQ_CU(launch_leaf_class(L, c, cl, cur_cnt.leaves[cl]));
-        radix_leaves |= cl == 3;
-      }
-      if (radix_leaves) SQ_CU(launch_fixup(L, c, nsm));
-      // nodes whose columns are sorted: pivots, counts, SkewTranspose, buckets
-      const u32 ready = cur_cnt.ready;
-      if (ready) {
-        const double re = spec.skew_only ? (double)spec.inst[0].n : (double)cur_cnt.ready_elems;
-        L.local.nodes += spec.skew_only ? 0 : ready;
-        L.begin(KF_PLAN);
-        k_plan<<<1, 1024, 0, st>>>(c, ready, K::key_words);
-        L.end();
-        SQ_CU(cudaGetLastError());
-        if (spec.skew_only) {
-          L.begin(KF_AUX);
-          k_put_pivots<DT><<<((u32)spec.k + 255) / 256, 256, 0, st>>>(
-              c, (const typename K::key_t *)spec.piv_keys, spec.piv_vals);
-          L.end();
-          SQ_CU(cudaGetLastError());
-        } else {
-          SQ_CU(launch_all_pivots(L, c, ready, cur_cnt.max_ready_k));
-        }
-        const u32 kmax = std::max<u32>(cur_cnt.max_ready_k, 2);
-        const size_t smem_count = (size_t)(kmax - 1) * sizeof(E) + (size_t)kmax * 4;
-        SQ_CU(set_smem(k_count<DT>, smem_count));
-        L.begin(KF_COUNT);
-        k_count<DT><<<grid_count, 1024, smem_count, st>>>(c, ready, kmax);
-        L.end();
-        L.local.bytes[KF_COUNT] += (KEY_BYTES + 4) * re;
-        SQ_CU(cudaGetLastError());
-        L.begin(KF_SCAN);
-        k_scan<<<grid_scan, 256, 0, st>>>(c, ready, K::key_words);
-        L.end();
-        SQ_CU(cudaGetLastError());
-        L.begin(KF_BSTART);
-        k_bstart<<<ready, 1024, 0, st>>>(c, ready, K::key_words);
-        L.end();
-        SQ_CU(cudaGetLastError());
-        const size_t smem_skew = sizeof(SkewSmem<DT, SKEW_CAP>);
-        SQ_CU(set_smem(k_skew<DT, SKEW_CAP>, smem_skew));
-        L.begin(KF_SKEW);
-        k_skew<DT, SKEW_CAP><<<grid_skew, 256, smem_skew, st>>>(c, ready);
-        L.end();
-        L.local.bytes[KF_SKEW] += 2.0 * (KEY_BYTES + 4) * re;
-        SQ_CU(cudaGetLastError());
-        if (spec.skew_only) {
-          L.begin(KF_AUX);
-          k_get_bstart<DT><<<((u32)spec.k + 256) / 256, 256, 0, st>>>(c, (u64 *)spec.bucket_start);
-          L.end();
-          SQ_CU(cudaGetLastError());
-        } else {
-          L.begin(KF_EXPAND);
-          k_expand_buckets<DT><<<grid_expand, 256, 0, st>>>(c, ready);
-          L.end();
-          SQ_CU(cudaGetLastError());
-        }
-      }
-      if (!spec.skew_only && (ready || cur_cnt.fresh)) {
-        L.begin(KF_EXPAND);
-        k_expand_cols<DT><<<grid_expand, 256, 0, st>>>(c);
-        L.end();
-        SQ_CU(cudaGetLastError());
-      }
-      SQ_CU(cudaMemcpyAsync(&hrb->cnt, cnt + nxt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
-      SQ_CU(cudaMemcpyAsync(&hrb->status, c.status, sizeof(Status), cudaMemcpyDeviceToHost, st));
+    // grows the node pool so that the next round cannot overflow it
+    auto grow_nodes = [&](u32 nodes_used) -> int {
+      if ((u64)nodes_used + fresh_cap <= node_cap || spec.skew_only) return 0;
+      const u64 ncap = std::max<u64>(2 * node_cap, (u64)nodes_used + 2 * fresh_cap);
+      Node *nn = nullptr;
+      SQ_CU(dalloc((void **)&nn, sizeof(Node) * ncap));
+      SQ_CU(cudaMemcpyAsync(nn, nodes, sizeof(Node) * nodes_used, cudaMemcpyDeviceToDevice, st));
       SQ_CU(cudaStreamSynchronize(st));
-      L.collect();
-      const Status &S = hrb->status;
-      if (S.error & ~ERRB_TRACE) {
-        snprintf(err, errlen, "engine error bits 0x%x (1 pivot attempts, 2 nodes, 4 list, 8 arena, 16 sizes)",
-                 S.error);
-        rc = (S.error & ERRB_ATTEMPTS) ? 7 : ((S.error & ERRB_SIZES) ? 8 : 2);
-        break;
+      free_guard.rel(nodes);
+      nodes = nn;
+      node_cap = ncap;
+      for (int q = 0; q < 2; q++) {
+        hctx[q].nodes = nodes;
+        hctx[q].node_cap = (u32)std::min<u64>(ncap, 0xffffffffull);
       }
-      done = S.done;
-      cur_cnt = hrb->cnt;
-      // grow the node pool so that the next round cannot overflow it
-      if ((u64)S.nodes_used + fresh_cap > node_cap && !spec.skew_only) {
-        const u64 ncap = std::max<u64>(2 * node_cap, (u64)S.nodes_used + 2 * fresh_cap);
-        Node *nn = nullptr;
-        SQ_CU(dalloc((void **)&nn, sizeof(Node) * ncap));
-        SQ_CU(cudaMemcpyAsync(nn, nodes, sizeof(Node) * S.nodes_used, cudaMemcpyDeviceToDevice, st));
+      SQ_CU(cudaMemcpyAsync(cdev, hctx, sizeof(hctx), cudaMemcpyHostToDevice, st));
+      return 0;
+    };
+    auto status_error = [&](const Status &S) -> int {
+      if (!(S.error & ~ERRB_TRACE)) return 0;
+      snprintf(err, errlen, "engine error bits 0x%x (1 pivot attempts, 2 nodes, 4 list, 8 arena, 16 sizes)",
+               S.error);
+      return (S.error & ERRB_ATTEMPTS) ? 7 : ((S.error & ERRB_SIZES) ? 8 : 2);
+    };
+    const bool graph = spec.graph && !spec.skew_only && !L.prof && done < ninst;
+    if (graph) {
+      // ---- every round on the device: one graph launch (relaunched only
+      // after the host has grown the node pool)
+      GraphSlot &G = graph_slot();
+      rc = graph_prepare(G, dev, nsm, err, errlen);
+      if (rc) return rc;
+      struct Back {
+        GraphStats gs;
+        Status status;
+      };
+      static_assert(sizeof(Back) <= 512, "read-back buffer contract");
+      void *pinned = nullptr;
+      SQ_CU(pinned_readback(&pinned));
+      Back &hb = *reinterpret_cast<Back *>(pinned);
+      for (;;) {
+        const int q = (int)(rounds & 1);
+        const Ctx pair[2] = {hctx[q], hctx[q ^ 1]};  // the body starts with the list parity of round `rounds`
+        GraphStats zero;
+        memset(&zero, 0, sizeof(zero));
+        SQ_CU(cudaMemcpyAsync(G.ctx, pair, sizeof(pair), cudaMemcpyHostToDevice, st));
+        SQ_CU(cudaMemcpyAsync(G.gs, &zero, sizeof(zero), cudaMemcpyHostToDevice, st));
+        SQ_CU(cudaGraphLaunch(G.exec, st));
+        SQ_CU(cudaMemcpyAsync(&hb.gs, G.gs, sizeof(GraphStats), cudaMemcpyDeviceToHost, st));
+        SQ_CU(cudaMemcpyAsync(&hb.status, c.status, sizeof(Status), cudaMemcpyDeviceToHost, st));
         SQ_CU(cudaStreamSynchronize(st));
-        free_guard.rel(nodes);
-        nodes = nn;
-        node_cap = ncap;
-        c.nodes = nodes;
-        c.node_cap = (u32)std::min<u64>(ncap, 0xffffffffull);
+        rounds += hb.gs.rounds;
+        L.local.nodes += hb.gs.nodes;
+        L.local.bytes[KF_LEAF] += 2.0 * (KEY_BYTES + 4) * (double)hb.gs.leaf_elems;
+        L.local.bytes[KF_COUNT] += (KEY_BYTES + 4) * (double)hb.gs.ready_elems;
+        L.local.bytes[KF_SKEW] += 2.0 * (KEY_BYTES + 4) * (double)hb.gs.ready_elems;
+        for (int f = 0; f < KF_COUNT_FAMILIES; f++) L.local.launches[f] += hb.gs.rounds * G.per_round.launches[f];
+        if ((rc = status_error(hb.status))) break;
+        if (hb.status.done >= ninst) break;
+        if (rounds >= kMaxRounds || !hb.gs.grow) {
+          snprintf(err, errlen, "recursion did not finish (%llu rounds)", (unsigned long long)rounds);
+          rc = 8;
+          break;
+        }
+        if ((rc = grow_nodes(hb.status.nodes_used))) return rc;
+      }
+    } else {
+      // ---- host-driven rounds: launches sized to the round's counts, read
+      // back after every round
+      struct Readback {
+        Counters cnt;
+        Status status;
+      };
+      static_assert(sizeof(Readback) <= 512, "read-back buffer contract");
+      Readback *hrb = reinterpret_cast<Readback *>(spec.host_readback);
+      if (!hrb) {
+        void *pinned = nullptr;
+        SQ_CU(pinned_readback(&pinned));
+        hrb = reinterpret_cast<Readback *>(pinned);
+      }
+      Counters cur_cnt = hc[0];
+      for (u32 r = 0;; r++) {
+        if (!spec.skew_only && done >= ninst) break;
+        if (spec.skew_only && r == 1) break;
+        if (r >= kMaxRounds) {
+          snprintf(err, errlen, "recursion did not finish");
+          rc = 8;
+          break;
+        }
+        rounds++;
+        const int cur = r & 1;
+        SQ_CU(issue_round(L, cdev + cur, &cur_cnt, A));
+        SQ_CU(cudaMemcpyAsync(&hrb->cnt, cnt + (cur ^ 1), sizeof(Counters), cudaMemcpyDeviceToHost, st));
+        SQ_CU(cudaMemcpyAsync(&hrb->status, c.status, sizeof(Status), cudaMemcpyDeviceToHost, st));
+        SQ_CU(cudaStreamSynchronize(st));
+        L.collect();
+        if ((rc = status_error(hrb->status))) break;
+        done = hrb->status.done;
+        cur_cnt = hrb->cnt;
+        if ((rc = grow_nodes(hrb->status.nodes_used))) return rc;
       }
     }
     if (rc == 0 && spec.trace && spec.trace_cap) {

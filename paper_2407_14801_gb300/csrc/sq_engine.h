@@ -37,6 +37,7 @@ struct InstSpec {
   uint32_t *dvals; // D vals scratch (device)
   uint64_t n;
   uint64_t seed;
+  uint32_t cutoff;  // 0: RunSpec::cutoff
 };
 
 struct TraceOut {
@@ -47,7 +48,7 @@ struct TraceOut {
 struct RunSpec {
   const InstSpec *inst;  // host array
   uint32_t ninst;
-  uint32_t cutoff;      // leaf iff n <= cutoff (2 <= cutoff <= max_leaf)
+  uint32_t cutoff;      // default leaf cutoff: leaf iff n <= cutoff (2 <= cutoff <= max_leaf)
   TraceOut *trace;      // host array (optional) receiving per-node records
   uint32_t trace_cap;
   uint32_t *trace_count;  // out
@@ -66,13 +67,16 @@ struct RunSpec {
   // Optional host buffer (any memory, >= 512 bytes) for the per-round
   // read-back; default: pinned memory from cudaMallocHost.
   void *host_readback;
+  // 1: run all rounds as one CUDA-graph launch (device-side loop) instead
+  // of one host round trip per round; ignored while profiling.
+  int graph;
 };
 
 // Device scratch bytes (slab + node record) of a stand-alone SkewTranspose.
 uint64_t engine_skew_scratch_bytes(int dtype, uint64_t n, uint64_t cols, uint64_t k);
 
 // Upper bound of the engine's own scratch bytes for a run (admission control).
-uint64_t engine_scratch_bytes(int dtype, uint64_t total_n, uint32_t ninst, uint32_t cutoff);
+uint64_t engine_scratch_bytes(int dtype, uint64_t total_n, uint32_t ninst, uint32_t cutoff, uint32_t cutoff_max);
 
 // Returns 0 or a status code (sq_status values); writes a message on error.
 int engine_run_u32(const RunSpec &spec, cudaStream_t st, char *err, size_t errlen);

@@ -30,8 +30,8 @@ uint32_t engine_max_leaf(int dtype) {
                          : (dtype == DT_U64 ? Engine<DT_U64>::max_leaf() : Engine<DT_F32>::max_leaf());
 }
 
-uint64_t engine_scratch_bytes_u64(uint64_t, uint32_t, uint32_t);
-uint64_t engine_scratch_bytes_f32(uint64_t, uint32_t, uint32_t);
+uint64_t engine_scratch_bytes_u64(uint64_t, uint32_t, uint32_t, uint32_t);
+uint64_t engine_scratch_bytes_f32(uint64_t, uint32_t, uint32_t, uint32_t);
 
 uint64_t engine_skew_scratch_bytes(int dtype, uint64_t n, uint64_t cols, uint64_t k) {
   if (dtype == DT_U64) return Engine<DT_U64>::skew_scratch_bytes(n, (u32)cols, (u32)k);
@@ -39,10 +39,10 @@ uint64_t engine_skew_scratch_bytes(int dtype, uint64_t n, uint64_t cols, uint64_
   return Engine<DT_U32>::skew_scratch_bytes(n, (u32)cols, (u32)k);
 }
 
-uint64_t engine_scratch_bytes(int dtype, uint64_t total_n, uint32_t ninst, uint32_t cutoff) {
-  if (dtype == DT_U64) return engine_scratch_bytes_u64(total_n, ninst, cutoff);
-  if (dtype == DT_F32) return engine_scratch_bytes_f32(total_n, ninst, cutoff);
-  return Engine<DT_U32>::scratch_bytes(total_n, ninst, cutoff);
+uint64_t engine_scratch_bytes(int dtype, uint64_t total_n, uint32_t ninst, uint32_t cutoff, uint32_t cutoff_max) {
+  if (dtype == DT_U64) return engine_scratch_bytes_u64(total_n, ninst, cutoff, cutoff_max);
+  if (dtype == DT_F32) return engine_scratch_bytes_f32(total_n, ninst, cutoff, cutoff_max);
+  return Engine<DT_U32>::scratch_bytes(total_n, ninst, cutoff, cutoff_max);
 }
 
 int engine_run_u32(const RunSpec &spec, cudaStream_t st, char *err, size_t errlen) {

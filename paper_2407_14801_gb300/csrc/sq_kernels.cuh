@@ -431,7 +431,8 @@ static __device__ void child_done(const Ctx &c, u32 parent, u32 kind, u32 inst) 
 // ---------------------------------------------------------------- leaves ---
 
 template <int DT, int T, int R, bool WARP>
-__global__ void __launch_bounds__(WARP ? 256 : T) k_leaf(Ctx c, int cls, u32 count) {
+__global__ void __launch_bounds__(WARP ? 256 : T) k_leaf(const Ctx *__restrict__ cp, int cls, u32 count) {
+  const Ctx &c = *cp;
   typedef KT<DT> K;
   typedef Sorter<K, T, R, WARP> S;
   typedef typename K::elem_t E;
@@ -441,21 +442,23 @@ __global__ void __launch_bounds__(WARP ? 256 : T) k_leaf(Ctx c, int cls, u32 cou
   constexpr int groups = WARP ? 8 : 1;
   const int g = WARP ? (threadIdx.x >> 5) : 0;
   const int tid = WARP ? (threadIdx.x & 31) : threadIdx.x;
-  const u32 li = blockIdx.x * groups + g;
-  if (li >= count) return;  // a whole warp (WARP) or the whole CTA
-  const Leaf L = c.leaves_cur[cls][li];
-  const Inst I = c.inst[L.inst];
-  E *s = smem + g * S::SMEM;
-  E x[R];
-  S::load(x, s, tid, (const key_t *)I.keys + L.off, I.vals + L.off, L.n);
-  S::sort(x, s, tid);
-  const u32 out = L.flags >> 8;
-  key_t *ok = (key_t *)(out ? I.dkeys : I.keys) + L.off;
-  u32 *ov = (out ? I.dvals : I.vals) + L.off;
-  S::store(x, s, tid, ok, ov, L.n);
-  if (tid == 0) {
-    __threadfence();
-    child_done(c, L.parent, L.flags & 0xffu, L.inst);
+  const u32 cnt = count != kDev ? count : min(c.cnt_cur->leaves[cls], c.leaf_cap[cls]);
+  // one leaf per warp (WARP) or per CTA; a fixed-size grid strides over the list
+  for (u32 li = blockIdx.x * groups + g; li < cnt; li += gridDim.x * groups) {
+    const Leaf L = c.leaves_cur[cls][li];
+    const Inst I = c.inst[L.inst];
+    E *s = smem + g * S::SMEM;
+    E x[R];
+    S::load(x, s, tid, (const key_t *)I.keys + L.off, I.vals + L.off, L.n);
+    S::sort(x, s, tid);
+    const u32 out = L.flags >> 8;
+    key_t *ok = (key_t *)(out ? I.dkeys : I.keys) + L.off;
+    u32 *ov = (out ? I.dvals : I.vals) + L.off;
+    S::store(x, s, tid, ok, ov, L.n);
+    if (tid == 0) {
+      __threadfence();
+      child_done(c, L.parent, L.flags & 0xffu, L.inst);
+    }
   }
 }
 
@@ -469,31 +472,33 @@ __global__ void __launch_bounds__(WARP ? 256 : T) k_leaf(Ctx c, int cls, u32 cou
 #endif
 template <int DT, int T, int R, int G>
 __global__ void __launch_bounds__(T, sizeof(typename KT<DT>::elem_t) == 8 ? SQ_RADIX_MINBLOCKS : 1)
-    k_leaf_radix(Ctx c, int cls, u32 count) {
+    k_leaf_radix(const Ctx *__restrict__ cp, int cls, u32 count) {
+  const Ctx &c = *cp;
   typedef KT<DT> K;
   typedef RadixSorter<K, T, R, G> RS;
   typedef typename K::key_t key_t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const u32 li = blockIdx.x / G;
-  if (li >= count) return;  // the whole cluster
+  const u32 cnt = count != kDev ? count : min(c.cnt_cur->leaves[cls], c.leaf_cap[cls]);
   const int tid = threadIdx.x, rank = RS::rank_in_cluster();
-  const Leaf L = c.leaves_cur[cls][li];
-  const Inst I = c.inst[L.inst];
-  const u64 off = L.off + (u64)rank * RS::NC;
-  const u32 nr = L.n > (u32)rank * RS::NC ? min((u32)RS::NC, L.n - (u32)rank * RS::NC) : 0u;
-  const u32 out = (L.flags >> 8) & 0xffu;
-  key_t kx[R];
-  u32 vx[R];
-  RS::load(kx, vx, tid, (const key_t *)I.keys + off, I.vals + off, nr);
-  const bool ok = RS::sort(kx, vx, smem_raw, tid, L.n);
-  RS::store(smem_raw, tid, (key_t *)(out ? I.dkeys : I.keys) + off, (out ? I.dvals : I.vals) + off, nr);
-  RS::cluster_sync();
-  if (rank == 0 && tid == 0) {
-    __threadfence();
-    if (ok)
-      child_done(c, L.parent, L.flags & 0xffu, L.inst);
-    else
-      push_fix(c, L);
+  for (u32 li = blockIdx.x / G; li < cnt; li += gridDim.x / G) {  // the whole cluster
+    const Leaf L = c.leaves_cur[cls][li];
+    const Inst I = c.inst[L.inst];
+    const u64 off = L.off + (u64)rank * RS::NC;
+    const u32 nr = L.n > (u32)rank * RS::NC ? min((u32)RS::NC, L.n - (u32)rank * RS::NC) : 0u;
+    const u32 out = (L.flags >> 8) & 0xffu;
+    key_t kx[R];
+    u32 vx[R];
+    RS::load(kx, vx, tid, (const key_t *)I.keys + off, I.vals + off, nr);
+    const bool ok = RS::sort(kx, vx, smem_raw, tid, L.n);
+    RS::store(smem_raw, tid, (key_t *)(out ? I.dkeys : I.keys) + off, (out ? I.dvals : I.vals) + off, nr);
+    RS::cluster_sync();
+    if (rank == 0 && tid == 0) {
+      __threadfence();
+      if (ok)
+        child_done(c, L.parent, L.flags & 0xffu, L.inst);
+      else
+        push_fix(c, L);
+    }
   }
 }
 
@@ -501,7 +506,8 @@ __global__ void __launch_bounds__(T, sizeof(typename KT<DT>::elem_t) == 8 ? SQ_R
 // sorts positions [rank*NC, (rank+1)*NC) of the leaf, then the cluster merges
 // through distributed shared memory (ClusterSorter).
 template <int DT, int T, int R, int G>
-__global__ void __launch_bounds__(T, 1) k_leaf_cluster(Ctx c, int cls, u32 count) {
+__global__ void __launch_bounds__(T, 1) k_leaf_cluster(const Ctx *__restrict__ cp, int cls, u32 count) {
+  const Ctx &c = *cp;
   typedef KT<DT> K;
   typedef ClusterSorter<K, T, R, G> CS;
   typedef typename CS::S S;
@@ -512,29 +518,31 @@ __global__ void __launch_bounds__(T, 1) k_leaf_cluster(Ctx c, int cls, u32 count
   E *s = reinterpret_cast<E *>(smem_raw);
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
-  const u32 li = blockIdx.x / G;
-  if (li >= count) return;  // the whole cluster
+  const u32 cnt = count != kDev ? count : min(c.cnt_cur->leaves[cls], c.leaf_cap[cls]);
   const int tid = threadIdx.x;
-  const Leaf L = c.leaves_cur[cls][li];
-  const Inst I = c.inst[L.inst];
-  const u64 off = L.off + (u64)rank * CS::NC;
-  const u32 nr = L.n > (u32)rank * CS::NC ? min((u32)CS::NC, L.n - (u32)rank * CS::NC) : 0u;
-  E x[R];
-  S::load(x, s, tid, (const key_t *)I.keys + off, I.vals + off, nr);
-  CS::sort(x, s, tid);
-  const u32 out = (L.flags >> 8) & 0xffu;
-  S::store(x, s, tid, (key_t *)(out ? I.dkeys : I.keys) + off, (out ? I.dvals : I.vals) + off, nr);
-  cl.sync();
-  if (rank == 0 && tid == 0) {
-    __threadfence();
-    child_done(c, L.parent, L.flags & 0xffu, L.inst);
+  for (u32 li = blockIdx.x / G; li < cnt; li += gridDim.x / G) {  // the whole cluster
+    const Leaf L = c.leaves_cur[cls][li];
+    const Inst I = c.inst[L.inst];
+    const u64 off = L.off + (u64)rank * CS::NC;
+    const u32 nr = L.n > (u32)rank * CS::NC ? min((u32)CS::NC, L.n - (u32)rank * CS::NC) : 0u;
+    E x[R];
+    S::load(x, s, tid, (const key_t *)I.keys + off, I.vals + off, nr);
+    CS::sort(x, s, tid);
+    const u32 out = (L.flags >> 8) & 0xffu;
+    S::store(x, s, tid, (key_t *)(out ? I.dkeys : I.keys) + off, (out ? I.dvals : I.vals) + off, nr);
+    cl.sync();
+    if (rank == 0 && tid == 0) {
+      __threadfence();
+      child_done(c, L.parent, L.flags & 0xffu, L.inst);
+    }
   }
 }
 
 // The (key, val) merge sort for leaves whose radix check failed: clusters of
 // G CTAs loop over the round's fix list; each leaf sits in its output buffer.
 template <int DT, int T, int R, int G>
-__global__ void __launch_bounds__(T, 1) k_fixup(Ctx c) {
+__global__ void __launch_bounds__(T, 1) k_fixup(const Ctx *__restrict__ cp) {
+  const Ctx &c = *cp;
   typedef KT<DT> K;
   typedef ClusterSorter<K, T, R, G> CS;
   typedef typename CS::S S;
@@ -573,7 +581,9 @@ __global__ void __launch_bounds__(T, 1) k_fixup(Ctx c) {
 
 // ------------------------------------------------------------------ plan ---
 
-static __global__ void __launch_bounds__(1024) k_plan(Ctx c, u32 ready_count, int kw) {
+static __global__ void __launch_bounds__(1024) k_plan(const Ctx *__restrict__ cp, u32 ready_count, int kw) {
+  const Ctx &c = *cp;
+  if (ready_count == kDev) ready_count = c.cnt_cur->ready;
   __shared__ u64 wt[33];
   __shared__ u64 carry[5];
   if (threadIdx.x < 5) carry[threadIdx.x] = 0;
@@ -628,29 +638,15 @@ static __global__ void __launch_bounds__(1024) k_plan(Ctx c, u32 ready_count, in
 // D with replacement, sort the drawn elements, and redraw the whole sample if
 // two are equal or the smallest is min(D) (the smallest column head).
 
-template <int DT, int T, int R, bool WARP>
-__global__ void __launch_bounds__(WARP ? 256 : T) k_pivots(Ctx c, u32 ready_count, u32 pmin, u32 pmax) {
-  typedef KT<DT> K;
-  typedef Sorter<K, T, R, WARP> S;
+template <class K, class S, int T, int R, bool WARP>
+__device__ __forceinline__ void pivots_node(const Ctx &c, Node *nd, typename K::elem_t *s, int tid) {
   typedef typename K::elem_t E;
   typedef typename K::key_t key_t;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  E *smem = reinterpret_cast<E *>(smem_raw);
-  constexpr int groups = WARP ? 8 : 1;
-  const int g = WARP ? (threadIdx.x >> 5) : 0;
-  const int tid = WARP ? (threadIdx.x & 31) : threadIdx.x;
-  const u32 ri = blockIdx.x * groups + g;
-  if (ri >= ready_count) return;
-  const u32 id = c.ready_cur[ri];
-  Node *nd = &c.nodes[id];
   const u32 np = nd->k - 1;  // pivots to draw
-  if (np <= pmin || np > pmax) return;
-  if (nd->meta + meta_layout(nd->k, nd->cols, nd->ncb, nd->nkb, K::key_words).total > c.meta_cap) return;
   const Inst I = c.inst[nd->inst];
   const key_t *dk = (const key_t *)I.dkeys + nd->off;
   const u32 *dv = I.dvals + nd->off;
   const u64 n = nd->n;
-  E *s = smem + g * S::SMEM;
 
   // min(D) over the column heads
   E mn = K::top();
@@ -734,11 +730,37 @@ __global__ void __launch_bounds__(WARP ? 256 : T) k_pivots(Ctx c, u32 ready_coun
           }
         }
       }
+      S::sync();  // the group is done with s before it takes the next node
       return;
     }
     S::sync();
   }
   if (tid == 0) atomicOr(&c.status->error, ERRB_ATTEMPTS);
+  S::sync();
+}
+
+template <int DT, int T, int R, bool WARP>
+__global__ void __launch_bounds__(WARP ? 256 : T) k_pivots(const Ctx *__restrict__ cp, u32 ready_count, u32 pmin, u32 pmax) {
+  const Ctx &c = *cp;
+  typedef KT<DT> K;
+  typedef Sorter<K, T, R, WARP> S;
+  typedef typename K::elem_t E;
+  typedef typename K::key_t key_t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  E *smem = reinterpret_cast<E *>(smem_raw);
+  constexpr int groups = WARP ? 8 : 1;
+  const int g = WARP ? (threadIdx.x >> 5) : 0;
+  const int tid = WARP ? (threadIdx.x & 31) : threadIdx.x;
+  if (ready_count == kDev) ready_count = min(c.cnt_cur->ready, c.ready_cap);
+  // one node per warp (WARP) or per CTA; a fixed-size grid strides over the list
+  for (u32 ri = blockIdx.x * groups + g; ri < ready_count; ri += gridDim.x * groups) {
+    const u32 id = c.ready_cur[ri];
+    Node *nd = &c.nodes[id];
+    const u32 np = nd->k - 1;  // pivots to draw
+    if (np <= pmin || np > pmax) continue;
+    if (nd->meta + meta_layout(nd->k, nd->cols, nd->ncb, nd->nkb, K::key_words).total > c.meta_cap) continue;
+    pivots_node<K, S, T, R, WARP>(c, nd, smem + g * S::SMEM, tid);
+  }
 }
 
 // ----------------------------------------------------------------- count ---
@@ -755,7 +777,9 @@ constexpr int kCountU = 4;
 constexpr u32 kPiece = 256;  // skew: elements per warp work piece
 
 template <int DT>
-__global__ void __launch_bounds__(1024) k_count(Ctx c, u32 ready_count, u32 kmax) {
+__global__ void __launch_bounds__(1024) k_count(const Ctx *__restrict__ cp, u32 ready_count, u32 kmax) {
+  const Ctx &c = *cp;
+  if (ready_count == kDev) ready_count = min(c.cnt_cur->ready, c.ready_cap);
   typedef KT<DT> K;
   typedef typename K::elem_t E;
   typedef typename K::key_t key_t;
@@ -877,7 +901,9 @@ __global__ void __launch_bounds__(1024) k_count(Ctx c, u32 ready_count, u32 kmax
 // T[I][j] -> exclusive prefix over I (in place); b[j] <- bucket size.
 // One work item = 32 buckets; 8 warps split the column blocks.
 
-static __global__ void __launch_bounds__(256) k_scan(Ctx c, u32 ready_count, int kw) {
+static __global__ void __launch_bounds__(256) k_scan(const Ctx *__restrict__ cp, u32 ready_count, int kw) {
+  const Ctx &c = *cp;
+  if (ready_count == kDev) ready_count = min(c.cnt_cur->ready, c.ready_cap);
   __shared__ u32 part[8][32];
   __shared__ u32 s_u, s_ri;
   const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
@@ -916,24 +942,28 @@ static __global__ void __launch_bounds__(256) k_scan(Ctx c, u32 ready_count, int
   }
 }
 
-// b[j] (sizes) -> bucket starts b[0..k]; one CTA per ready node.
-static __global__ void __launch_bounds__(1024) k_bstart(Ctx c, u32 ready_count, int kw) {
+// b[j] (sizes) -> bucket starts b[0..k]; one CTA per ready node at a time.
+static __global__ void __launch_bounds__(1024) k_bstart(const Ctx *__restrict__ cp, u32 ready_count, int kw) {
+  const Ctx &c = *cp;
   __shared__ u32 wt[33];
-  const Node nd = c.nodes[c.ready_cur[blockIdx.x]];
-  const MetaLayout ML = meta_layout(nd.k, nd.cols, nd.ncb, nd.nkb, kw);
-  u32 *b = c.meta + nd.meta + ML.b;
-  u32 carry = 0;
-  for (u32 base = 0; base < nd.k; base += blockDim.x) {
-    const u32 j = base + threadIdx.x;
-    const u32 v = j < nd.k ? b[j] : 0;
-    u32 tot;
-    const u32 ex = block_excl_scan_u32(v, wt, tot);
-    if (j < nd.k) b[j] = carry + ex;
-    carry += tot;
-  }
-  if (threadIdx.x == 0) {
-    b[nd.k] = carry;
-    if (carry != nd.n) atomicOr(&c.status->error, ERRB_SIZES);
+  if (ready_count == kDev) ready_count = min(c.cnt_cur->ready, c.ready_cap);
+  for (u32 ri = blockIdx.x; ri < ready_count; ri += gridDim.x) {
+    const Node nd = c.nodes[c.ready_cur[ri]];
+    const MetaLayout ML = meta_layout(nd.k, nd.cols, nd.ncb, nd.nkb, kw);
+    u32 *b = c.meta + nd.meta + ML.b;
+    u32 carry = 0;
+    for (u32 base = 0; base < nd.k; base += blockDim.x) {
+      const u32 j = base + threadIdx.x;
+      const u32 v = j < nd.k ? b[j] : 0;
+      u32 tot;
+      const u32 ex = block_excl_scan_u32(v, wt, tot);
+      if (j < nd.k) b[j] = carry + ex;
+      carry += tot;
+    }
+    if (threadIdx.x == 0) {
+      b[nd.k] = carry;
+      if (carry != nd.n) atomicOr(&c.status->error, ERRB_SIZES);
+    }
   }
 }
 
@@ -979,7 +1009,9 @@ __device__ __forceinline__ u32 warp_excl_scan(u32 v, u32 &total) {
 }
 
 template <int DT, int CAP>
-__global__ void __launch_bounds__(256) k_skew(Ctx c, u32 ready_count) {
+__global__ void __launch_bounds__(256) k_skew(const Ctx *__restrict__ cp, u32 ready_count) {
+  const Ctx &c = *cp;
+  if (ready_count == kDev) ready_count = min(c.cnt_cur->ready, c.ready_cap);
   typedef KT<DT> K;
   typedef typename K::elem_t E;
   typedef typename K::key_t key_t;
@@ -1179,7 +1211,7 @@ static __device__ void spawn_batch(const Ctx &c, bool has, const Child &ch, u32 
   int cls = -1;
   u32 local = 0;
   if (has) {
-    cls = ch.n <= c.cutoff ? class_of(ch.n, nclass) : kLeafClasses;
+    cls = ch.n <= c.inst[ch.inst].cutoff ? class_of(ch.n, nclass) : kLeafClasses;
     local = atomicAdd(&ccount[cls], 1u);
     atomicAdd(&celems[cls], (u64)ch.n);
   }
@@ -1245,7 +1277,9 @@ static __device__ void spawn_batch(const Ctx &c, bool has, const Child &ch, u32 
 // non-empty (bucket j >= 1 holds pivot j, bucket 0 the minimum), so the node
 // waits for exactly k children.
 template <int DT>
-__global__ void __launch_bounds__(256) k_expand_buckets(Ctx c, u32 ready_count) {
+__global__ void __launch_bounds__(256) k_expand_buckets(const Ctx *__restrict__ cp, u32 ready_count) {
+  const Ctx &c = *cp;
+  if (ready_count == kDev) ready_count = min(c.cnt_cur->ready, c.ready_cap);
   __shared__ u32 s_u, s_ri;
   for (;;) {
     grab_item(c, &c.status->cur_ebkt, c.status->echunks, 3, ready_count, &s_u, &s_ri);
@@ -1284,7 +1318,8 @@ __global__ void __launch_bounds__(256) k_expand_buckets(Ctx c, u32 ready_count) 
 // Column children of every new node (Algorithm 1's first loop); new internal
 // column nodes are expanded in the next round.
 template <int DT>
-__global__ void __launch_bounds__(256) k_expand_cols(Ctx c) {
+__global__ void __launch_bounds__(256) k_expand_cols(const Ctx *__restrict__ cp) {
+  const Ctx &c = *cp;
   __shared__ u32 s_u;
   for (;;) {
     if (threadIdx.x == 0) s_u = atomicAdd(&c.status->cur_expand, 1u);
@@ -1317,11 +1352,57 @@ __global__ void __launch_bounds__(256) k_expand_cols(Ctx c) {
   }
 }
 
+// ------------------------------------------------------- round control ---
+
+// Start of a round: zero the next round's counters and this round's work
+// cursors (the pointers come from the round's context, so the same launch
+// serves every run).
+static __global__ void k_round_begin(const Ctx *__restrict__ cp) {
+  const Ctx &c = *cp;
+  constexpr u32 nc = sizeof(Counters) / 4;
+  u32 *z = reinterpret_cast<u32 *>(c.cnt_nxt);
+  for (u32 i = threadIdx.x; i < nc; i += blockDim.x) z[i] = 0;
+  u32 *cur = &c.status->cur_count;
+  if (threadIdx.x < 7) cur[threadIdx.x] = 0;
+}
+
+// Totals of a graph-launched run (a host-driven run counts on the host).
+struct GraphStats {
+  unsigned long long rounds, nodes, leaf_elems, ready_elems;
+  u32 grow;  // the loop stopped because the node pool needs to grow
+  u32 pad;
+};
+
+// End of a round of a graph-launched run: add the round's work to the
+// totals and set the loop condition -- another round runs unless every
+// instance is done, an error is latched, the node pool must grow first (the
+// host grows it and relaunches), or the round limit is reached.  `next` is
+// the condition of the body's second round (0 when this is that round).
+static __global__ void k_round_end(const Ctx *__restrict__ cp, cudaGraphConditionalHandle loop,
+                                   cudaGraphConditionalHandle next, int has_next, GraphStats *gs,
+                                   unsigned long long max_rounds) {
+  const Ctx &c = *cp;
+  const Counters &C = *c.cnt_cur;
+  unsigned long long le = 0;
+  for (int cl = 0; cl < kLeafClasses; cl++) le += C.leaf_elems[cl];
+  gs->rounds += 1;
+  gs->nodes += C.ready;
+  gs->leaf_elems += le;
+  gs->ready_elems += C.ready_elems;
+  const Status &S = *c.status;
+  const bool grow = (u64)S.nodes_used + c.fresh_cap > c.node_cap;
+  if (grow) gs->grow = 1;
+  const bool more = !(S.error & ~ERRB_TRACE) && S.done < c.ninst && !grow && gs->rounds < max_rounds;
+  cudaGraphSetConditional(loop, more ? 1u : 0u);
+  if (has_next) cudaGraphSetConditional(next, more ? 1u : 0u);
+}
+
 // ------------------------------------------------ stand-alone SkewTranspose ---
 
 // Caller-supplied pivots -> the node's metadata.
 template <int DT>
-__global__ void k_put_pivots(Ctx c, const typename KT<DT>::key_t *pk, const u32 *pv) {
+__global__ void k_put_pivots(const Ctx *__restrict__ cp, const typename KT<DT>::key_t *pk, const u32 *pv) {
+  const Ctx &c = *cp;
   const Node &nd = c.nodes[c.ready_cur[0]];
   const MetaLayout ML = meta_layout(nd.k, nd.cols, nd.ncb, nd.nkb, KT<DT>::key_words);
   const u32 j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1333,7 +1414,8 @@ __global__ void k_put_pivots(Ctx c, const typename KT<DT>::key_t *pk, const u32 
 
 // Bucket starts b[0..k] -> the caller's 64-bit array.
 template <int DT>
-__global__ void k_get_bstart(Ctx c, u64 *out) {
+__global__ void k_get_bstart(const Ctx *__restrict__ cp, u64 *out) {
+  const Ctx &c = *cp;
   const Node &nd = c.nodes[c.ready_cur[0]];
   const MetaLayout ML = meta_layout(nd.k, nd.cols, nd.ncb, nd.nkb, KT<DT>::key_words);
   const u32 j = blockIdx.x * blockDim.x + threadIdx.x;

@@ -88,7 +88,7 @@ extern "C" sq_status sq_skew_transpose_noalloc(const sq_skew_buf *buf, uint64_t 
   }
   Bump bump{static_cast<char *>(base), kNoAllocScratchBytes, 0};
   alignas(64) unsigned char readback[512];
-  sq::InstSpec is;
+  sq::InstSpec is{};
   is.keys = buf->keys_out;
   is.vals = buf->vals_out;
   is.dkeys = const_cast<void *>(buf->keys_in);

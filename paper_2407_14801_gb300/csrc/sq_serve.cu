@@ -76,15 +76,20 @@ namespace {
 
 uint64_t scratch_need(sq_server *s, const std::vector<Req *> &b, int dtype) {
   uint64_t tot = 0;
-  uint32_t cnt = 0;
+  uint32_t cnt = 0, c = s->cutoff ? s->cutoff : sq_get_cutoff((sq_dtype)dtype), cmax = c;
   for (Req *r : b)
     if (r->d.dtype == dtype) {
       tot += r->d.n;
       cnt++;
+      // work lists are sized for the smallest cutoff, leaf classes for the largest
+      if (!s->cutoff) {
+        const uint32_t ci = sq_cutoff_for((sq_dtype)dtype, r->d.n);
+        c = std::min(c, ci);
+        cmax = std::max(cmax, ci);
+      }
     }
   if (!cnt) return 0;
-  const uint32_t c = s->cutoff ? s->cutoff : sq_get_cutoff((sq_dtype)dtype);
-  return sq::engine_scratch_bytes(dtype, tot, cnt, c) + 4096;
+  return sq::engine_scratch_bytes(dtype, tot, cnt, c, cmax) + 4096;
 }
 
 uint64_t batch_scratch(sq_server *s, const std::vector<Req *> &b) {
@@ -125,13 +130,14 @@ void run_batch(sq_server *s, cudaStream_t st, std::vector<Req *> &batch, uint64_
       if (r->d.dtype != d || r->d.n == 0) continue;
       const uint64_t n = r->d.n, w = kbytes(r->d.dtype);
       char *base = s->slab + r->off;
-      sq::InstSpec x;
+      sq::InstSpec x{};
       x.keys = base;
       x.vals = (uint32_t *)(base + al(n * w));
       x.dkeys = base + al(n * w) + al(n * 4);
       x.dvals = (uint32_t *)(base + al(n * w) + al(n * 4) + al(n * w));
       x.n = n;
       x.seed = r->d.seed;
+      x.cutoff = s->cutoff ? s->cutoff : sq_cutoff_for((sq_dtype)d, n);
       is.push_back(x);
       who.push_back(q);
     }
@@ -150,6 +156,7 @@ void run_batch(sq_server *s, cudaStream_t st, std::vector<Req *> &batch, uint64_
     spec.inst = is.data();
     spec.ninst = (uint32_t)is.size();
     spec.cutoff = s->cutoff ? s->cutoff : sq_get_cutoff((sq_dtype)d);
+    spec.graph = sq_get_launch_mode() != SQ_LAUNCH_HOST;
     spec.dev_alloc = bump_alloc;
     spec.dev_free = bump_free;
     spec.alloc_ctx = &bump;

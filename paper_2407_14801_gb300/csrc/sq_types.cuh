@@ -169,6 +169,8 @@ struct Inst {
   void *dkeys; // D keys (scratch)
   u32 *dvals;  // D vals (scratch)
   u64 n;
+  u32 cutoff;  // leaf iff a node's n <= cutoff (per instance)
+  u32 pad;
 };
 
 // A SquareSort call with n > cutoff (or a stand-alone SkewTranspose).
@@ -225,6 +227,10 @@ struct TraceRec {
   u32 depth, kind, attempts, index;
 };
 
+// A launch's item count that the kernel reads from the round's counters
+// (graph-launched rounds, whose launches do not change from run to run).
+constexpr u32 kDev = 0xffffffffu;
+
 // Tile geometry (count blocks, skew tiles).
 constexpr int kCountCols = 16;  // columns per count unit (block-total granularity)
 constexpr int kSkewCols = 32;   // columns per skew tile (multiple of kCountCols)
@@ -257,6 +263,7 @@ struct Ctx {
   u32 fix_cap;
   u32 class_cap[kLeafClasses];  // max elements per leaf class
   int recurse;                  // 0 for a stand-alone SkewTranspose
+  u32 ninst;                    // instances of the run
 };
 
 // Metadata layout of a ready node (32-bit words from Node::meta), each

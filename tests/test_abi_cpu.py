@@ -63,3 +63,11 @@ def test_rejects_bad_arguments_without_a_device(sq):
     assert L.sq_set_cutoff(0, 300) == 0 and L.sq_get_cutoff(0) == 300
     assert L.sq_set_cutoff(0, 0) == 0 and L.sq_get_cutoff(0) == 65536
     assert L.sq_sort(None, None, 0, 0, 0, None) == 0  # empty sort is a no-op
+
+
+def test_launch_mode_without_a_device(sq):
+    L = sq.lib()
+    assert L.sq_get_launch_mode() == 2  # auto
+    assert L.sq_set_launch_mode(5) == 1 and b"launch mode" in L.sq_last_error()
+    assert L.sq_set_launch_mode(0) == 0 and L.sq_get_launch_mode() == 0
+    assert L.sq_set_launch_mode(2) == 0

@@ -150,3 +150,38 @@ def test_serve_budget_and_errors(sq):
             srv.poll(12345)
     finally:
         srv.close()
+
+
+def test_cutoff_table_applies_per_instance(sq):
+    """A cutoff table picks each instance's cutoff by its size, in single
+    sorts and inside one batch: the recursion (trace, node count) is the
+    oracle's at that cutoff."""
+    table = {9: 64, 11: 512, 13: 2048, 15: 16384}
+    try:
+        sq.set_cutoff("u32", 0)
+        sq.set_cutoff_table("u32", table)
+        sizes = [600, 1000, 3000, 4095, 9000, 12000, 40000, 65000, 520, 2100]
+        srcs = [W.uniform_u32(n, 70 + i) for i, n in enumerate(sizes)]
+        want_nodes = 0
+        for i, s in enumerate(srcs):
+            c = table[max(k for k in table if (1 << k) <= s.size)]
+            assert sq.cutoff_for("u32", s.size) == c
+            ok, ov, otr, _ = oracle.sort(s, W.iota(s.size), seed=i, cutoff=c, trace_cap=1 << 16)
+            want_nodes += len(otr)
+            k = torch.from_numpy(s.view(np.int32).copy()).cuda()
+            v = torch.arange(s.size, dtype=torch.int32).cuda()
+            tr = sq.sort(k, v, seed=i, dtype="u32", trace_cap=1 << 16)
+            key = lambda r: (r["off"], r["depth"], r["kind"], r["index"])
+            assert sorted(tr, key=key) == sorted(otr, key=key)
+        batch = [(torch.from_numpy(s.view(np.int32).copy()).cuda(), torch.arange(s.size, dtype=torch.int32).cuda(), i)
+                 for i, s in enumerate(srcs)]
+        before = sq.stats()["nodes"]
+        sq.sort_batch(batch)
+        assert sq.stats()["nodes"] - before == want_nodes
+        for (bk, bv, i), s in zip(batch, srcs):
+            ok, ov, _, _ = oracle.sort(s, W.iota(s.size), seed=i, cutoff=64)
+            assert same(bk.cpu().numpy().view(np.uint32), ok, "u32")
+            assert (bv.cpu().numpy().view(np.uint32) == ov).all()
+    finally:
+        sq.set_cutoff_table("u32", [])
+        sq.load_tuning()
