@@ -39,6 +39,12 @@ struct Engine {
   static constexpr int NCLASS = LeafCfg<DT>::nclass;
   static constexpr int SKEW_CAP = sizeof(E) == 8 ? 2048 : 1024;
   static constexpr size_t KEY_BYTES = sizeof(typename K::key_t);
+  // Leaf sorts of float32 keys use the one-word element (NaN bits restored
+  // by the leaf kernels, or the leaf left to the fix list).
+  static constexpr int LDT = DT == DT_F32 ? DT_F32W : DT;
+  typedef KT<LDT> KL;
+  typedef typename KL::elem_t EL;
+  static constexpr bool kFix = KL::lossy;  // leaves may go to the fix list
   static constexpr u32 kHostExpandCols = 2048;  // roots with this many columns are expanded on the host
 
   static u32 max_leaf() { return class_cap(NCLASS - 1); }
@@ -119,9 +125,9 @@ struct Engine {
 
   template <int T, int R, bool WARP>
   static cudaError_t launch_leaf(Launcher &L, const Ctx *cp, int cls, u32 count, int nsm) {
-    typedef Sorter<K, T, R, WARP> S;
-    const size_t smem = (size_t)(WARP ? 8 : 1) * S::SMEM * sizeof(E);
-    auto kern = k_leaf<DT, T, R, WARP>;
+    typedef Sorter<KL, T, R, WARP> S;
+    const size_t smem = (size_t)(WARP ? 8 : 1) * (S::SMEM * sizeof(EL) + (KL::lossy ? 4 * kNanWords : 0));
+    auto kern = k_leaf<LDT, T, R, WARP>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
     const int threads = WARP ? 256 : T;
@@ -153,28 +159,9 @@ struct Engine {
   }
 
   template <int T, int R, int G>
-  static cudaError_t launch_leaf_radix(Launcher &L, const Ctx *cp, int cls, u32 count, int nsm) {
-    const size_t smem = RadixSorter<K, T, R, G>::kSmem;
-    auto kern = k_leaf_radix<DT, T, R, G>;
-    cudaError_t e = set_smem(kern, smem);
-    if (e != cudaSuccess) return e;
-    L.begin(KF_LEAF);
-    if (G == 1) {
-      const u32 grid = count == kDev ? fill_grid(kern, T, smem, nsm) : count;
-      kern<<<grid, T, smem, L.st>>>(cp, cls, count);
-      e = cudaGetLastError();
-    } else {
-      const u32 grid = count == kDev ? fill_clusters(kern, T, smem, G, nsm) : count * G;
-      e = launch_cluster(kern, dim3(grid, 1, 1), T, smem, G, L.st, cp, cls, count);
-    }
-    L.end();
-    return e;
-  }
-
-  template <int T, int R, int G>
   static cudaError_t launch_leaf_cluster(Launcher &L, const Ctx *cp, int cls, u32 count, int nsm) {
-    const size_t smem = sizeof(E) * (size_t)Sorter<K, T, R, false>::SMEM;
-    auto kern = k_leaf_cluster<DT, T, R, G>;
+    const size_t smem = sizeof(EL) * (size_t)Sorter<KL, T, R, false>::SMEM + (KL::lossy ? 4 * kNanWords : 0);
+    auto kern = k_leaf_cluster<LDT, T, R, G>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
     const u32 grid = count == kDev ? fill_clusters(kern, T, smem, G, nsm) : count * G;
@@ -189,20 +176,14 @@ struct Engine {
       case 0: return launch_leaf<32, 2, true>(L, cp, 0, count, nsm);
       case 1: return launch_leaf<32, 16, true>(L, cp, 1, count, nsm);
       case 2: return launch_leaf<128, 16, false>(L, cp, 2, count, nsm);
-      case 3: return launch_leaf_radix<512, 16, 1>(L, cp, 3, count, nsm);
-      case 4:
-        if constexpr (sizeof(E) == 8) return launch_leaf<1024, 16, false>(L, cp, 4, count, nsm);
-        else return launch_leaf_cluster<512, 16, 2>(L, cp, 4, count, nsm);
-      case 5:
-        if constexpr (sizeof(E) == 8) return launch_leaf_cluster<1024, 16, 2>(L, cp, 5, count, nsm);
-        else return launch_leaf_cluster<512, 16, 4>(L, cp, 5, count, nsm);
-      default:
-        if constexpr (sizeof(E) == 8) return launch_leaf_cluster<1024, 16, 4>(L, cp, 6, count, nsm);
-        else return launch_leaf_cluster<512, 16, 8>(L, cp, 6, count, nsm);
+      case 3: return launch_leaf<512, 16, false>(L, cp, 3, count, nsm);
+      case 4: return launch_leaf_cluster<512, 16, 2>(L, cp, 4, count, nsm);
+      case 5: return launch_leaf_cluster<512, 16, 4>(L, cp, 5, count, nsm);
+      default: return launch_leaf_cluster<512, 16, 8>(L, cp, 6, count, nsm);
     }
   }
 
-  // The (key, val) merge sort of leaves whose radix check failed this round.
+  // The (key, val) merge sort of this round's fix list.
   static cudaError_t launch_fixup(Launcher &L, const Ctx *cp, int nsm) {
     constexpr bool wide = sizeof(E) == 8;
     constexpr int T = wide ? 1024 : 512, R = 16, G = wide ? 4 : 8;
@@ -271,15 +252,15 @@ struct Engine {
     k_round_begin<<<1, 64, 0, st>>>(cp);
     L.end();
     SQ_TRY(cudaGetLastError());
-    bool radix_leaves = false;
+    bool any_leaves = false;
     for (int cl = 0; cl < NCLASS; cl++) {
       const u32 n = hc ? hc->leaves[cl] : kDev;
       if (!n) continue;
       if (hc) L.local.bytes[KF_LEAF] += 2.0 * (KEY_BYTES + 4) * (double)hc->leaf_elems[cl];
       SQ_TRY(launch_leaf_class(L, cp, cl, n, nsm));
-      radix_leaves |= cl == 3;
+      any_leaves = true;
     }
-    if (radix_leaves) SQ_TRY(launch_fixup(L, cp, nsm));
+    if (kFix && any_leaves) SQ_TRY(launch_fixup(L, cp, nsm));
     const u32 ready = hc ? hc->ready : kDev;
     if (ready) {
       const double re = A.skew_only ? A.skew_elems : (hc ? (double)hc->ready_elems : 0.0);
@@ -532,8 +513,9 @@ struct Engine {
     P.o_done = carve(4 * (size_t)std::max<u32>(ninst, 1));
     P.o_trace = carve(sizeof(TraceRec) * (size_t)trace_cap);
     P.o_wbase = carve(4 * 4 * P.ready_cap);
-    P.fix_cap = 0;
-    for (int c = 3; c < kLeafClasses; c++) P.fix_cap += P.leaf_cap[c];
+    P.fix_cap = 0;  // any leaf of a lossy element type may go to the fix list
+    if (kFix)
+      for (int c = 0; c < kLeafClasses; c++) P.fix_cap += P.leaf_cap[c];
     P.o_fix = carve(sizeof(Leaf) * (size_t)P.fix_cap);
     P.o_ctx = carve(2 * sizeof(Ctx));
     P.slab_bytes = off;

@@ -27,9 +27,10 @@ template <int DT>
 struct LeafCfg;
 // Leaf classes (elements per class): c0 = warp x 2 (64), c1 = warp x 16
 // (512), c2 = 128 x 16 (2048), c3 = 512 x 16 (8192), c4 = 16384, c5 = 32768,
-// c6 = 65536.  c3 is a radix sort on one CTA of 512 x 16; c4..c6 are merge
-// sorts on one CTA of 1024 x 16 and clusters of 2 and 4 of them (uint32
-// keys), or on clusters of 2, 4 and 8 CTAs of 512 x 16.  Pivot samples use the single-CTA sorters only.
+// c6 = 65536.  All are merge sorts: c0..c3 on one warp or one CTA, c4..c6 on
+// clusters of 2, 4 and 8 CTAs of 512 x 16 whose cross-CTA rounds copy each
+// CTA's merge window out of the others' shared memory.  Pivot samples use
+// the single-CTA sorters only.
 template <>
 struct LeafCfg<DT_U32> {
   static constexpr int nclass = 7;
@@ -179,219 +180,8 @@ __device__ __forceinline__ void grab_item(const Ctx &c, u32 *cursor, u32 total, 
   }
 }
 
-// ------------------------------------------------------------ radix leaf ---
-// Leaf sort by a stable least-significant-digit radix sort of the key
-// ordinals (8-bit digits, one pass per key byte), on one CTA (G = 1) or on a
-// cluster of G CTAs whose shared memories hold consecutive parts of the leaf.
-// A pass ranks every CTA's elements warp by warp (peers with the same digit
-// found by __match_any_sync, in sequence order, one shared atomic per digit
-// group), adds the per-digit totals of the lower-ranked CTAs (read through
-// distributed shared memory) and of the lower digits, and scatters each
-// element straight into the shared memory of the CTA that owns its new
-// position.  A stable key sort equals the (key, val) order exactly when,
-// among equal keys, vals already increase with position -- true at every
-// level of the recursion when vals are the original index.  The result is
-// checked; a leaf that fails is re-sorted by the (key, val) merge sort.
-template <class K, int T, int R, int G>
-struct RadixSorter {
-  typedef typename K::key_t key_t;
-  typedef typename K::elem_t E;
-  static constexpr int W = T / 32;
-  static constexpr int NC = T * R;  // elements per CTA
-  static constexpr int RADIX = 256;
-  static constexpr int PASSES = (int)sizeof(typename K::ord_t);
-  static constexpr int CS = W + 1;  // padded counter row: (digit, warp) at d*CS + w
-  static constexpr size_t kValsOff = sizeof(key_t) * (size_t)NC;
-  static constexpr size_t kCntOff = kValsOff + 4 * (size_t)NC;
-  static constexpr size_t kTotOff = kCntOff + 4 * (size_t)RADIX * CS;
-  static constexpr size_t kBaseOff = kTotOff + 4 * (size_t)RADIX;
-  static constexpr size_t kScanOff = kBaseOff + 4 * (size_t)RADIX;
-  static constexpr size_t kFlagOff = kScanOff + 4 * 40;
-  static constexpr size_t kSmem = kFlagOff + 16;
-  static_assert(R % 4 == 0 && T >= RADIX && T % 32 == 0, "one thread per digit; ranks and digits packed");
-
-  __device__ __forceinline__ static u32 digit(key_t k, int pass) {
-    return (u32)((u64)K::ord_key(k) >> (8 * pass)) & (RADIX - 1);
-  }
-  __device__ __forceinline__ static int striped(int tid, int q) { return (tid >> 5) * (R * 32) + q * 32 + (tid & 31); }
-  __device__ __forceinline__ static int rank_in_cluster() {
-    if constexpr (G > 1)
-      return (int)cooperative_groups::this_cluster().block_rank();
-    else
-      return 0;
-  }
-  __device__ __forceinline__ static void cluster_sync() {
-    if constexpr (G > 1)
-      cooperative_groups::this_cluster().sync();
-    else
-      __syncthreads();
-  }
-  template <class P>
-  __device__ __forceinline__ static P *peer(P *p, int r) {
-    if constexpr (G > 1)
-      return cooperative_groups::this_cluster().map_shared_rank(p, r);
-    else
-      return p;
-  }
-
-  // Loads this CTA's part (n elements) into the warp-striped register layout.
-  __device__ static void load(key_t (&kx)[R], u32 (&vx)[R], int tid, const key_t *keys, const u32 *vals, u32 n) {
-#pragma unroll
-    for (int q = 0; q < R; q++) {
-      const int p = striped(tid, q);
-      const bool in = (u32)p < n;
-      kx[q] = in ? keys[p] : K::pad_key();
-      vx[q] = in ? vals[p] : 0xffffffffu;
-    }
-  }
-
-  // Sorts the G*NC elements (the leaf's first n are real); afterwards CTA r
-  // holds sorted positions [r*NC, (r+1)*NC) in its shared memory.  Returns
-  // whether the leaf is in (key, val) order (same answer in every CTA).
-  __device__ static bool sort(key_t (&kx)[R], u32 (&vx)[R], unsigned char *smem, int tid, u32 n) {
-    key_t *sk = reinterpret_cast<key_t *>(smem);
-    u32 *sv = reinterpret_cast<u32 *>(smem + kValsOff);
-    u32 *cnt = reinterpret_cast<u32 *>(smem + kCntOff);
-    u32 *tot = reinterpret_cast<u32 *>(smem + kTotOff);
-    u32 *base = reinterpret_cast<u32 *>(smem + kBaseOff);
-    u32 *scan = reinterpret_cast<u32 *>(smem + kScanOff);
-    u32 *flag = reinterpret_cast<u32 *>(smem + kFlagOff);
-    const int lane = tid & 31, w = tid >> 5, rank = rank_in_cluster();
-    const u32 lt = (1u << lane) - 1u;
-#pragma unroll 1
-    for (int pass = 0; pass < PASSES; pass++) {
-      for (int i = tid; i < RADIX * CS; i += T) cnt[i] = 0;
-      __syncthreads();
-      u32 rk[R / 2], dg[R / 4];  // ranks (2 x 16 bits) and digits (4 x 8 bits) per register
-#pragma unroll
-      for (int q = 0; q < R; q++) {
-        // rank among this warp's elements with the same digit, in sequence
-        // order: the lowest peer reserves the group's slots, all read its base
-        const u32 d = digit(kx[q], pass);
-        if (q & 3)
-          dg[q >> 2] |= d << ((q & 3) * 8);
-        else
-          dg[q >> 2] = d;
-#if SQ_RADIX_BALLOT
-        u32 peers = 0xffffffffu;  // lanes whose digit equals mine, one ballot per digit bit
-#pragma unroll
-        for (int bit = 0; bit < 8; bit++) {
-          const u32 m = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
-          peers &= ((d >> bit) & 1u) ? m : ~m;
-        }
-#else
-        const u32 peers = __match_any_sync(0xffffffffu, d);
-#endif
-        const u32 before = __popc(peers & lt);
-        const int leader = __ffs(peers) - 1;
-        u32 b = 0;
-        if (before == 0) b = atomicAdd(&cnt[d * CS + w], (u32)__popc(peers));
-        b = __shfl_sync(0xffffffffu, b, leader);
-        const u32 r = b + before;
-        if (q & 1)
-          rk[q >> 1] |= r << 16;
-        else
-          rk[q >> 1] = r;
-      }
-      __syncthreads();
-      if (tid < RADIX) {  // per digit: offsets of this CTA's warps, and its total
-        u32 run = 0;
-        for (int ww = 0; ww < W; ww++) {
-          const u32 c = cnt[tid * CS + ww];
-          cnt[tid * CS + ww] = run;
-          run += c;
-        }
-        tot[tid] = run;
-      }
-      cluster_sync();
-      u32 all = 0, lower = 0;
-      if (tid < RADIX) {  // this digit over the cluster, and over lower-ranked CTAs
-#pragma unroll
-        for (int r = 0; r < G; r++) {
-          const u32 v = (r == rank) ? tot[tid] : *peer(tot + tid, r);
-          all += v;
-          if (r < rank) lower += v;
-        }
-      }
-      u32 digits_total;
-      const u32 ex = block_excl_scan_u32(all, scan, digits_total);
-      if (tid < RADIX) base[tid] = ex + lower;
-      __syncthreads();
-#pragma unroll
-      for (int q = 0; q < R; q++) {
-        const u32 d = (dg[q >> 2] >> ((q & 3) * 8)) & 0xffu;
-        const u32 pos = base[d] + cnt[d * CS + w] + ((rk[q >> 1] >> ((q & 1) * 16)) & 0xffffu);
-        const int owner = G > 1 ? (int)(pos / NC) : 0;
-        const u32 lp = G > 1 ? pos - (u32)owner * NC : pos;
-        if (G == 1 || owner == rank) {
-          sk[lp] = kx[q];
-          sv[lp] = vx[q];
-        } else {
-          *peer(sk + lp, owner) = kx[q];
-          *peer(sv + lp, owner) = vx[q];
-        }
-      }
-      cluster_sync();
-      if (pass + 1 < PASSES) {
-#pragma unroll
-        for (int q = 0; q < R; q++) {
-          const int p = striped(tid, q);
-          kx[q] = sk[p];
-          vx[q] = sv[p];
-        }
-      }
-    }
-    // (key, val) order check over the leaf's first n positions
-    bool bad = false;
-    const u32 g0 = (u32)rank * NC;
-#pragma unroll 4
-    for (int q = 0; q < R; q++) {
-      const u32 i = (u32)tid * R + q;
-      const u32 gi = g0 + i;
-      if (gi + 1 < n) {
-        key_t k1;
-        u32 v1;
-        if (i + 1 < (u32)NC) {
-          k1 = sk[i + 1];
-          v1 = sv[i + 1];
-        } else {
-          k1 = *peer(sk, rank + 1);
-          v1 = *peer(sv, rank + 1);
-        }
-        if (K::ord_key(sk[i]) == K::ord_key(k1) && sv[i] > v1) bad = true;
-      }
-    }
-    bad = __syncthreads_or(bad);
-    if constexpr (G == 1) {
-      return !bad;
-    } else {
-      if (tid == 0) *flag = bad ? 1u : 0u;
-      cluster_sync();
-      u32 any = 0;
-#pragma unroll
-      for (int r = 0; r < G; r++) any |= *peer(flag, r);
-      cluster_sync();  // peers' flags read before anyone leaves or reuses them
-      return any == 0;
-    }
-  }
-
-  // Coalesced store of this CTA's part (its first nr positions).
-  __device__ static void store(unsigned char *smem, int tid, key_t *keys, u32 *vals, u32 nr) {
-    const key_t *sk = reinterpret_cast<const key_t *>(smem);
-    const u32 *sv = reinterpret_cast<const u32 *>(smem + kValsOff);
-#pragma unroll
-    for (int q = 0; q < R; q++) {
-      const int p = q * T + tid;
-      if ((u32)p < nr) {
-        keys[p] = sk[p];
-        vals[p] = sv[p];
-      }
-    }
-  }
-};
-
-// Appends a leaf whose radix result failed the (key, val) check; it is
-// sorted again, in place in its output buffer, by k_fixup later this round.
+// A leaf that its leaf kernel could not sort exactly goes to this round's
+// fix list, which k_fixup sorts with the (key, val) merge sort.
 __device__ __forceinline__ void push_fix(const Ctx &c, Leaf L) {
   const u32 i = atomicAdd(&c.status->fix_count, 1u);
   L.flags |= LEAF_IN_OUT;
@@ -430,8 +220,48 @@ static __device__ void child_done(const Ctx &c, u32 parent, u32 kind, u32 inst) 
 
 // ---------------------------------------------------------------- leaves ---
 
+// Keys whose bits the leaf element does not keep (K::lossy: NaN float32
+// keys) are listed per leaf in shared memory while the leaf is loaded: the
+// count, then kNanCap vals and kNanCap keys.  After the sort they sit at the
+// end of the leaf in val order (every NaN has the largest ordinal, ties go
+// by val) and get their bits back.  A leaf with more such keys is copied to
+// its output and left to the fix list's exact (key, val) sort.
+constexpr u32 kNanCap = 64;
+constexpr u32 kNanWords = 1 + 2 * kNanCap;
+
+template <class K>
+__device__ __forceinline__ void nan_note(u32 *nl, typename K::key_t k, u32 v) {
+  if constexpr (K::lossy) {
+    if (!K::exact(k)) {
+      const u32 i = atomicAdd(&nl[0], 1u);
+      if (i < kNanCap) {
+        nl[1 + i] = v;
+        nl[1 + kNanCap + i] = (u32)k;
+      }
+    }
+  }
+}
+
+// Rank of list entry i among all listed keys: by val, then (list, entry).
+__device__ __forceinline__ u32 nan_rank(const u32 *nl, u32 cnt, u32 v, u32 i) {
+  u32 r = 0;
+  for (u32 j = 0; j < cnt; j++) {
+    const u32 vj = nl[1 + j];
+    r += (vj < v) || (vj == v && j < i);
+  }
+  return r;
+}
+
+// CTAs per SM the one-CTA leaf kernels are built for (a register budget):
+// with 8-byte elements about 80 registers a thread for the small classes,
+// 64 for the 512-thread class.
+template <int DT, int T, bool WARP>
+constexpr int kLeafMinBlocks() {
+  return sizeof(typename KT<DT>::elem_t) != 8 ? 1 : WARP ? 3 : T <= 128 ? 6 : T >= 512 ? 2 : 1;
+}
+
 template <int DT, int T, int R, bool WARP>
-__global__ void __launch_bounds__(WARP ? 256 : T) k_leaf(const Ctx *__restrict__ cp, int cls, u32 count) {
+__global__ void __launch_bounds__(WARP ? 256 : T, kLeafMinBlocks<DT, T, WARP>()) k_leaf(const Ctx *__restrict__ cp, int cls, u32 count) {
   const Ctx &c = *cp;
   typedef KT<DT> K;
   typedef Sorter<K, T, R, WARP> S;
@@ -442,6 +272,7 @@ __global__ void __launch_bounds__(WARP ? 256 : T) k_leaf(const Ctx *__restrict__
   constexpr int groups = WARP ? 8 : 1;
   const int g = WARP ? (threadIdx.x >> 5) : 0;
   const int tid = WARP ? (threadIdx.x & 31) : threadIdx.x;
+  u32 *nl = reinterpret_cast<u32 *>(smem + groups * S::SMEM) + g * kNanWords;  // K::lossy only
   const u32 cnt = count != kDev ? count : min(c.cnt_cur->leaves[cls], c.leaf_cap[cls]);
   // one leaf per warp (WARP) or per CTA; a fixed-size grid strides over the list
   for (u32 li = blockIdx.x * groups + g; li < cnt; li += gridDim.x * groups) {
@@ -449,12 +280,38 @@ __global__ void __launch_bounds__(WARP ? 256 : T) k_leaf(const Ctx *__restrict__
     const Inst I = c.inst[L.inst];
     E *s = smem + g * S::SMEM;
     E x[R];
-    S::load(x, s, tid, (const key_t *)I.keys + L.off, I.vals + L.off, L.n);
-    S::sort(x, s, tid);
     const u32 out = L.flags >> 8;
+    const key_t *ik = (const key_t *)I.keys + L.off;
+    const u32 *iv = I.vals + L.off;
     key_t *ok = (key_t *)(out ? I.dkeys : I.keys) + L.off;
     u32 *ov = (out ? I.dvals : I.vals) + L.off;
+    u32 nn = 0;
+    if constexpr (K::lossy) {
+      if (tid == 0) nl[0] = 0;
+      S::sync();
+    }
+    S::load(x, s, tid, ik, iv, L.n, [&](key_t k, u32 v) { nan_note<K>(nl, k, v); });
+    if constexpr (K::lossy) {
+      nn = nl[0];
+      S::sync();  // read before the list is reset for the group's next leaf
+      if (nn > kNanCap) {
+        if (out)
+          for (u32 p = tid; p < L.n; p += T) {
+            ok[p] = ik[p];
+            ov[p] = iv[p];
+          }
+        if (tid == 0) push_fix(c, L);
+        continue;
+      }
+    }
+    S::sort(x, s, tid);
     S::store(x, s, tid, ok, ov, L.n);
+    if constexpr (K::lossy) {
+      if (nn) {
+        for (u32 i = tid; i < nn; i += T) ok[L.n - nn + nan_rank(nl, nn, nl[1 + i], i)] = (key_t)nl[1 + kNanCap + i];
+        S::sync();
+      }
+    }
     if (tid == 0) {
       __threadfence();
       child_done(c, L.parent, L.flags & 0xffu, L.inst);
@@ -462,51 +319,14 @@ __global__ void __launch_bounds__(WARP ? 256 : T) k_leaf(const Ctx *__restrict__
   }
 }
 
-// A leaf of a radix class: one CTA (G = 1) or a cluster of G CTAs, CTA
-// `rank` holding positions [rank*NC, (rank+1)*NC) of the leaf.
-#ifndef SQ_RADIX_BALLOT
-#define SQ_RADIX_BALLOT 1  // peer masks from per-bit ballots rather than __match_any_sync
+#ifndef SQ_CLUSTER_MINB
+#define SQ_CLUSTER_MINB 2  // CTAs per SM the 512-thread 8-byte-element cluster kernels are built for
 #endif
-#ifndef SQ_RADIX_MINBLOCKS
-#define SQ_RADIX_MINBLOCKS 2  // CTAs per SM the 8-byte-element radix kernels are built for
-#endif
-template <int DT, int T, int R, int G>
-__global__ void __launch_bounds__(T, sizeof(typename KT<DT>::elem_t) == 8 ? SQ_RADIX_MINBLOCKS : 1)
-    k_leaf_radix(const Ctx *__restrict__ cp, int cls, u32 count) {
-  const Ctx &c = *cp;
-  typedef KT<DT> K;
-  typedef RadixSorter<K, T, R, G> RS;
-  typedef typename K::key_t key_t;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const u32 cnt = count != kDev ? count : min(c.cnt_cur->leaves[cls], c.leaf_cap[cls]);
-  const int tid = threadIdx.x, rank = RS::rank_in_cluster();
-  for (u32 li = blockIdx.x / G; li < cnt; li += gridDim.x / G) {  // the whole cluster
-    const Leaf L = c.leaves_cur[cls][li];
-    const Inst I = c.inst[L.inst];
-    const u64 off = L.off + (u64)rank * RS::NC;
-    const u32 nr = L.n > (u32)rank * RS::NC ? min((u32)RS::NC, L.n - (u32)rank * RS::NC) : 0u;
-    const u32 out = (L.flags >> 8) & 0xffu;
-    key_t kx[R];
-    u32 vx[R];
-    RS::load(kx, vx, tid, (const key_t *)I.keys + off, I.vals + off, nr);
-    const bool ok = RS::sort(kx, vx, smem_raw, tid, L.n);
-    RS::store(smem_raw, tid, (key_t *)(out ? I.dkeys : I.keys) + off, (out ? I.dvals : I.vals) + off, nr);
-    RS::cluster_sync();
-    if (rank == 0 && tid == 0) {
-      __threadfence();
-      if (ok)
-        child_done(c, L.parent, L.flags & 0xffu, L.inst);
-      else
-        push_fix(c, L);
-    }
-  }
-}
-
 // A leaf of a cluster merge class: CTA `rank` of the cluster loads and
 // sorts positions [rank*NC, (rank+1)*NC) of the leaf, then the cluster merges
 // through distributed shared memory (ClusterSorter).
 template <int DT, int T, int R, int G>
-__global__ void __launch_bounds__(T, 1) k_leaf_cluster(const Ctx *__restrict__ cp, int cls, u32 count) {
+__global__ void __launch_bounds__(T, (T <= 512 && sizeof(typename KT<DT>::elem_t) == 8) ? SQ_CLUSTER_MINB : 1) k_leaf_cluster(const Ctx *__restrict__ cp, int cls, u32 count) {
   const Ctx &c = *cp;
   typedef KT<DT> K;
   typedef ClusterSorter<K, T, R, G> CS;
@@ -520,17 +340,67 @@ __global__ void __launch_bounds__(T, 1) k_leaf_cluster(const Ctx *__restrict__ c
   const int rank = (int)cl.block_rank();
   const u32 cnt = count != kDev ? count : min(c.cnt_cur->leaves[cls], c.leaf_cap[cls]);
   const int tid = threadIdx.x;
+  u32 *nl = reinterpret_cast<u32 *>(s + S::SMEM);  // K::lossy only: this CTA's part's NaN list
   for (u32 li = blockIdx.x / G; li < cnt; li += gridDim.x / G) {  // the whole cluster
     const Leaf L = c.leaves_cur[cls][li];
     const Inst I = c.inst[L.inst];
     const u64 off = L.off + (u64)rank * CS::NC;
     const u32 nr = L.n > (u32)rank * CS::NC ? min((u32)CS::NC, L.n - (u32)rank * CS::NC) : 0u;
-    E x[R];
-    S::load(x, s, tid, (const key_t *)I.keys + off, I.vals + off, nr);
-    CS::sort(x, s, tid);
     const u32 out = (L.flags >> 8) & 0xffu;
-    S::store(x, s, tid, (key_t *)(out ? I.dkeys : I.keys) + off, (out ? I.dvals : I.vals) + off, nr);
+    const key_t *ik = (const key_t *)I.keys + L.off;
+    const u32 *iv = I.vals + L.off;
+    key_t *ok = (key_t *)(out ? I.dkeys : I.keys) + L.off;
+    u32 *ov = (out ? I.dvals : I.vals) + L.off;
+    const u32 q0 = (u32)rank * CS::NC;  // this CTA's part of the leaf: [q0, q0 + nr)
+    E x[R];
+    u32 nn = 0, total = 0;
+    if constexpr (K::lossy) {
+      if (tid == 0) nl[0] = 0;
+      __syncthreads();
+    }
+    S::load(x, s, tid, ik + q0, iv + q0, nr, [&](key_t k, u32 v) { nan_note<K>(nl, k, v); });
+    if constexpr (K::lossy) {
+      cl.sync();  // every part's list is complete
+      u32 most = 0;
+      for (int r = 0; r < G; r++) {
+        const u32 m = *cl.map_shared_rank(nl, r);
+        total += m;
+        most = max(most, m);
+      }
+      nn = nl[0];
+      cl.sync();  // the counts are read before any list changes
+      if (most > kNanCap) {  // too many to restore: the fix list sorts the leaf
+        if (out)
+          for (u32 p = tid; p < nr; p += T) {
+            ok[q0 + p] = ik[q0 + p];
+            ov[q0 + p] = iv[q0 + p];
+          }
+        cl.sync();
+        if (rank == 0 && tid == 0) push_fix(c, L);
+        continue;
+      }
+    }
+    CS::sort(x, s, tid, (int)L.n);
+    S::store(x, s, tid, ok + q0, ov + q0, nr);
     cl.sync();
+    if constexpr (K::lossy) {
+      if (total) {  // the leaf's NaNs end it, in val order (then by part, entry)
+        for (u32 i = tid; i < nn; i += T) {
+          const u32 v = nl[1 + i];
+          u32 r = 0;
+          for (int q = 0; q < G; q++) {
+            const u32 *ql = cl.map_shared_rank(nl, q);
+            const u32 qn = ql[0];
+            for (u32 j = 0; j < qn; j++) {
+              const u32 vj = ql[1 + j];
+              r += (vj < v) || (vj == v && (q < rank || (q == rank && j < i)));
+            }
+          }
+          ok[L.n - total + r] = (key_t)nl[1 + kNanCap + i];
+        }
+        cl.sync();  // the lists are read before the next leaf resets them
+      }
+    }
     if (rank == 0 && tid == 0) {
       __threadfence();
       child_done(c, L.parent, L.flags & 0xffu, L.inst);
@@ -538,8 +408,9 @@ __global__ void __launch_bounds__(T, 1) k_leaf_cluster(const Ctx *__restrict__ c
   }
 }
 
-// The (key, val) merge sort for leaves whose radix check failed: clusters of
-// G CTAs loop over the round's fix list; each leaf sits in its output buffer.
+// The (key, val) merge sort of the round's fix list (leaves a leaf kernel
+// could not sort exactly): clusters of G CTAs loop over the list; each leaf
+// sits in its output buffer.
 template <int DT, int T, int R, int G>
 __global__ void __launch_bounds__(T, 1) k_fixup(const Ctx *__restrict__ cp) {
   const Ctx &c = *cp;
@@ -569,7 +440,7 @@ __global__ void __launch_bounds__(T, 1) k_fixup(const Ctx *__restrict__ cp) {
     const u32 nr = L.n > (u32)off ? min((u32)CS::NC, L.n - (u32)off) : 0u;
     E x[R];
     S::load(x, s, tid, kk + off, vv + off, nr);
-    CS::sort(x, s, tid);
+    CS::sort(x, s, tid, (int)L.n);
     S::store(x, s, tid, kk + off, vv + off, nr);
     cl.sync();
     if (rank == 0 && tid == 0) {

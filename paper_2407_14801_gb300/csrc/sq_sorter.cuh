@@ -43,6 +43,55 @@ __device__ __forceinline__ typename K::elem_t warp_min(typename K::elem_t v) {
   return v;
 }
 
+#ifndef SQ_MERGE_LOOKAHEAD
+#define SQ_MERGE_LOOKAHEAD 0  // elements of each run held ahead of its head (shared memory)
+#endif
+#ifndef SQ_CLUSTER_LOOKAHEAD
+#define SQ_CLUSTER_LOOKAHEAD 0  // the same for runs read from other CTAs' shared memory
+#endif
+constexpr int kLookahead = SQ_MERGE_LOOKAHEAD;
+constexpr int kClusterLookahead = SQ_CLUSTER_LOOKAHEAD;
+
+// One thread's part of a merge round: R outputs of the merge of runs A and
+// B (wa and wb elements) starting at A[ai], B[bi] (its merge-path split).
+// Besides its head, each run keeps the next D elements in registers, so the
+// load issued when a run advances is needed only D steps later and the
+// merge's compare-select chain does not wait on load latency.  get(run, i)
+// reads element i of run 0 (A) or 1 (B).
+template <class K, int R, int D, class Get>
+__device__ __forceinline__ void serial_merge(typename K::elem_t (&x)[R], int ai, int bi, int wa, int wb, Get get) {
+  typedef typename K::elem_t E;
+  E a[D + 1], b[D + 1];
+#pragma unroll
+  for (int j = 0; j <= D; j++) {
+    a[j] = ai + j < wa ? get(0, ai + j) : K::top();
+    b[j] = bi + j < wb ? get(1, bi + j) : K::top();
+  }
+#pragma unroll
+  for (int k = 0; k < R; k++) {
+    const bool tb = (bi < wb) && (ai >= wa || K::lt(b[0], a[0]));
+    x[k] = tb ? b[0] : a[0];
+    if (k + 1 < R) {
+      E nv = K::top();
+      if (k + D + 1 < R) {  // a value loaded now is used D+1 steps later at the earliest
+        const int ni = (tb ? bi : ai) + D + 1;
+        const bool in = ni < (tb ? wb : wa);
+        nv = get(tb ? 1 : 0, in ? ni : 0);
+        nv = in ? nv : K::top();
+      }
+#pragma unroll
+      for (int j = 0; j < D; j++) {
+        a[j] = tb ? a[j] : a[j + 1];
+        b[j] = tb ? b[j + 1] : b[j];
+      }
+      a[D] = tb ? a[D] : nv;
+      b[D] = tb ? nv : b[D];
+      ai += tb ? 0 : 1;
+      bi += tb ? 1 : 0;
+    }
+  }
+}
+
 // T threads (T == 32 and WARP: one warp of a larger CTA), R elements each.
 template <class K, int T, int R, bool WARP>
 struct Sorter {
@@ -107,25 +156,8 @@ struct Sorter {
         else
           lo = mid + 1;
       }
-      int ai = lo, bi = diag - lo;
-      E av = ai < w ? s[px(base + ai)] : K::top();
-      E bv = bi < w ? s[px(bb + bi)] : K::top();
-#pragma unroll
-      for (int k = 0; k < R; k++) {
-        const bool tb = (bi < w) && (ai >= w || K::lt(bv, av));
-        x[k] = tb ? bv : av;
-        if (k + 1 < R) {  // advance the consumed run; one unconditional load
-          const int ni = (tb ? bi : ai) + 1;
-          const bool in = ni < w;
-          const int addr = (tb ? bb : base) + (in ? ni : 0);
-          E nv = s[px(addr)];
-          nv = in ? nv : K::top();
-          ai = tb ? ai : ni;
-          bi = tb ? ni : bi;
-          av = tb ? av : nv;
-          bv = tb ? nv : bv;
-        }
-      }
+      serial_merge<K, R, kLookahead>(x, lo, diag - lo, w, w,
+                                     [&](int run, int i) { return s[px((run ? bb : base) + i)]; });
       if (warp_local)
         __syncwarp();
       else
@@ -137,10 +169,23 @@ struct Sorter {
   // blocked register layout; positions >= n become top().
   __device__ static void load(E (&x)[R], E *s, int tid, const typename K::key_t *keys, const u32 *vals,
                               u32 n) {
+    load(x, s, tid, keys, vals, n, [](typename K::key_t, u32) {});
+  }
+  // The same, calling obs(key, val) for every element loaded.
+  template <class Obs>
+  __device__ static void load(E (&x)[R], E *s, int tid, const typename K::key_t *keys, const u32 *vals, u32 n,
+                              Obs obs) {
 #pragma unroll
     for (int k = 0; k < R; k++) {
       const int p = k * T + tid;
-      s[px(p)] = (u32)p < n ? K::make(keys[p], vals[p]) : K::top();
+      if ((u32)p < n) {
+        const typename K::key_t kk = keys[p];
+        const u32 vv = vals[p];
+        obs(kk, vv);
+        s[px(p)] = K::make(kk, vv);
+      } else {
+        s[px(p)] = K::top();
+      }
     }
     sync();
 #pragma unroll
@@ -178,53 +223,96 @@ struct ClusterSorter {
   static constexpr int NC = T * R;  // elements per CTA
   static constexpr int N = NC * G;
 
-  __device__ static void sort(E (&x)[R], E *s, int tid) {
+  // n: valid elements of the whole leaf (the rest top(), as left by
+  // S::load).
+  __device__ static void sort(E (&x)[R], E *s, int tid, int n = N) {
     S::sort(x, s, tid);
-    merge_rounds(x, s, tid);
+    merge_rounds(x, s, tid, n);
   }
 
   // The cross-CTA rounds only: x holds this CTA's sorted run, blocked.
-  __device__ static void merge_rounds(E (&x)[R], E *s, int tid) {
+  // In a round merging runs of w elements, this CTA produces outputs
+  // [rank*NC, rank*NC + NC) of its pair of runs A, B.  Two warps find the
+  // merge-path splits of that window's ends by 32-way searches over the
+  // other CTAs' shared memory; every thread then copies window elements
+  // (coalesced distributed-shared-memory loads, no dependent chains) into
+  // registers; after a cluster barrier the window goes to this CTA's own
+  // shared memory (the A part, then the B part) and is merged locally like
+  // an in-CTA round.
+  // A CTA whose outputs all lie at positions >= n (top() only) keeps its
+  // shared memory (top() since load) and only takes part in the barriers.
+  __device__ static void merge_rounds(E (&x)[R], E *s, int tid, int n = N) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
+    __shared__ int split[2];
     const int rank = (int)cl.block_rank();
+    const int lane = tid & 31, warp = tid >> 5;
+    const bool idle = rank * NC >= n;
     auto at = [&](int gi) -> E { return *cl.map_shared_rank(s + S::px(gi % NC), gi / NC); };
 #pragma unroll 1
     for (int w = NC; w < N; w <<= 1) {
+      if (idle) {  // the same barriers as the others, nothing else
+        cl.sync();
+        __syncthreads();
+        cl.sync();
+        __syncthreads();
+        __syncthreads();
+        continue;
+      }
 #pragma unroll
       for (int k = 0; k < R; k++) s[S::px(tid * R + k)] = x[k];
       cl.sync();
-      const int p0 = rank * NC + tid * R;
+      const int p0 = rank * NC;
       const int base = p0 & ~(2 * w - 1);
-      const int diag = p0 - base;
       const int bb = base + w;
-      int lo = diag > w ? diag - w : 0, hi = diag < w ? diag : w;
+      if (warp < 2) {
+        // smallest i in [lo, hi] with B[d-1-i] < A[i] (hi if none): i elements
+        // of the first d outputs come from A
+        const int d = p0 - base + warp * NC;
+        int lo = d > w ? d - w : 0, hi = d < w ? d : w;
+        while (hi - lo > 32) {
+          const int step = (hi - lo + 31) / 32;
+          const int q = lo + lane * step;
+          const bool p = q < hi && K::lt(at(bb + d - 1 - q), at(base + q));
+          const unsigned m = __ballot_sync(0xffffffffu, p);
+          const int last = min(31, (hi - 1 - lo) / step);  // last probe inside [lo, hi)
+          const int f = m ? __ffs(m) - 1 : 32;
+          const int nlo = f == 0 ? lo : lo + (min(f, last + 1) - 1) * step + 1;
+          const int nhi = f == 32 ? hi : lo + f * step;
+          lo = nlo;
+          hi = nhi;
+        }
+        const int q = lo + lane;
+        const bool p = q < hi && K::lt(at(bb + d - 1 - q), at(base + q));
+        const unsigned m = __ballot_sync(0xffffffffu, p);
+        if (lane == 0) split[warp] = m ? lo + __ffs(m) - 1 : hi;
+      }
+      __syncthreads();
+      const int d0 = p0 - base;
+      const int a0 = split[0], a1 = split[1];
+      const int b0 = d0 - a0;
+      const int la = a1 - a0;  // window: A[a0, a1) then B[b0, b0 + NC - la)
+#pragma unroll
+      for (int k = 0; k < R; k++) {
+        const int e = k * T + tid;
+        x[k] = at(e < la ? base + a0 + e : bb + b0 + (e - la));
+      }
+      cl.sync();  // every CTA has copied its window: shared memory may be overwritten
+#pragma unroll
+      for (int k = 0; k < R; k++) s[S::px(k * T + tid)] = x[k];
+      __syncthreads();
+      const int lb = NC - la, dd = tid * R;
+      int lo = dd > lb ? dd - lb : 0, hi = dd < la ? dd : la;
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (K::lt(at(bb + diag - 1 - mid), at(base + mid)))
+        if (K::lt(s[S::px(la + dd - 1 - mid)], s[S::px(mid)]))
           hi = mid;
         else
           lo = mid + 1;
       }
-      int ai = lo, bi = diag - lo;
-      E av = ai < w ? at(base + ai) : K::top();
-      E bv = bi < w ? at(bb + bi) : K::top();
-#pragma unroll
-      for (int k = 0; k < R; k++) {
-        const bool tb = (bi < w) && (ai >= w || K::lt(bv, av));
-        x[k] = tb ? bv : av;
-        if (k + 1 < R) {
-          const int ni = (tb ? bi : ai) + 1;
-          const bool in = ni < w;
-          E nv = at((tb ? bb : base) + (in ? ni : 0));
-          nv = in ? nv : K::top();
-          ai = tb ? ai : ni;
-          bi = tb ? ni : bi;
-          av = tb ? av : nv;
-          bv = tb ? nv : bv;
-        }
-      }
-      cl.sync();  // every CTA has read its runs before they are overwritten
+      serial_merge<K, R, kLookahead>(x, lo, dd - lo, la, lb,
+                                     [&](int run, int i) { return s[S::px((run ? la : 0) + i)]; });
+      __syncthreads();  // the window is read before the next round (or the store) overwrites it
     }
   }
 };

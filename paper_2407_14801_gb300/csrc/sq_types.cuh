@@ -9,7 +9,9 @@ namespace sq {
 typedef unsigned long long u64;
 typedef uint32_t u32;
 
-enum : int { DT_U32 = 0, DT_U64 = 1, DT_F32 = 2 };
+enum : int { DT_U32 = 0, DT_U64 = 1, DT_F32 = 2, DT_F32W = 3 };
+// DT_F32W: float32 keys held as one 64-bit compare word in the leaf sorts
+// (exact for every key but NaN; the leaf kernels restore NaN bits).
 
 // Status bits latched by kernels in Status::error.
 enum : u32 {
@@ -38,6 +40,9 @@ __host__ __device__ __forceinline__ u32 f32_ordinal(u32 b) {
   return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
 }
 
+// Inverse of f32_ordinal on non-NaN keys (a NaN maps to 0x7fffffff).
+__host__ __device__ __forceinline__ u32 f32_from_ordinal(u32 o) { return (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o; }
+
 // Three-word element: 64-bit compare word plus a 32-bit word.
 struct __align__(16) E3 {
   u64 k;
@@ -55,6 +60,8 @@ struct KT<DT_U32> {
   typedef u64 elem_t;
   typedef u32 ord_t;
   static constexpr int key_words = 1;
+  static constexpr bool lossy = false;
+  __device__ __forceinline__ static bool exact(key_t) { return true; }
   __device__ __forceinline__ static ord_t ord_key(key_t k) { return k; }
   __device__ __forceinline__ static key_t pad_key() { return 0xffffffffu; }
   __device__ __forceinline__ static elem_t make(key_t k, u32 v) { return ((u64)k << 32) | v; }
@@ -72,6 +79,8 @@ struct KT<DT_F32> {
   typedef E3 elem_t;
   typedef u32 ord_t;
   static constexpr int key_words = 1;
+  static constexpr bool lossy = false;
+  __device__ __forceinline__ static bool exact(key_t) { return true; }
   __device__ __forceinline__ static ord_t ord_key(key_t k) { return f32_ordinal(k); }
   __device__ __forceinline__ static key_t pad_key() { return 0xffffffffu; }  // a NaN: ordinal max
   __device__ __forceinline__ static elem_t make(key_t k, u32 v) {
@@ -94,6 +103,27 @@ struct KT<DT_F32> {
   }
 };
 
+// float32 keys in leaf sorts: the compare word alone, key bits recovered
+// from the ordinal.  NaN keys are not recovered (every NaN has one
+// ordinal): `lossy` tells the leaf kernels to record and restore them.
+template <>
+struct KT<DT_F32W> {
+  typedef u32 key_t;
+  typedef u64 elem_t;
+  typedef u32 ord_t;
+  static constexpr int key_words = 1;
+  static constexpr bool lossy = true;
+  __device__ __forceinline__ static bool exact(key_t k) { return (k & 0x7fffffffu) <= 0x7f800000u; }
+  __device__ __forceinline__ static ord_t ord_key(key_t k) { return f32_ordinal(k); }
+  __device__ __forceinline__ static key_t pad_key() { return 0xffffffffu; }
+  __device__ __forceinline__ static elem_t make(key_t k, u32 v) { return ((u64)f32_ordinal(k) << 32) | v; }
+  __device__ __forceinline__ static key_t key(elem_t e) { return f32_from_ordinal((u32)(e >> 32)); }
+  __device__ __forceinline__ static u32 val(elem_t e) { return (u32)e; }
+  __device__ __forceinline__ static bool lt(elem_t a, elem_t b) { return a < b; }
+  __device__ __forceinline__ static bool eq(elem_t a, elem_t b) { return a == b; }
+  __device__ __forceinline__ static elem_t top() { return ~0ull; }
+};
+
 // uint64 keys: (key, val) compared lexicographically.
 template <>
 struct KT<DT_U64> {
@@ -101,6 +131,8 @@ struct KT<DT_U64> {
   typedef E3 elem_t;
   typedef u64 ord_t;
   static constexpr int key_words = 2;
+  static constexpr bool lossy = false;
+  __device__ __forceinline__ static bool exact(key_t) { return true; }
   __device__ __forceinline__ static ord_t ord_key(key_t k) { return k; }
   __device__ __forceinline__ static key_t pad_key() { return ~0ull; }
   __device__ __forceinline__ static elem_t make(key_t k, u32 v) {

@@ -168,3 +168,25 @@ def test_empty_and_tiny(sq):
         keys = W.uniform_u32(n, 3)
         gk, gv, _ = gpu_sort(sq, keys, W.iota(n), "u32", 1, 2, trace=False)
         assert (gk == np.sort(keys)).all()
+
+
+@pytest.mark.parametrize("n", [60, 500, 2000, 8000, 16000, 30000, 65536])
+def test_f32_leaf_nan_bits_restored(sq, n):
+    """Single-leaf float32 sorts with 0, 1, a few, exactly 64, 65 and many NaNs
+    of random sign and payload: the leaf kernels hold float keys as one
+    compare word and restore NaN bits afterwards (or hand the leaf to the
+    exact fix-up sort), so every NaN must come back bit for bit."""
+    rng = np.random.default_rng(n)
+    for nan_count in (0, 1, 7, 64, 65, 300, n):
+        if nan_count > n:
+            continue
+        keys = W.normal_f32(n, n + nan_count, p_inf=0.01, p_negzero=0.01, p_nan=0.0)
+        where = rng.choice(n, size=nan_count, replace=False)
+        bits = keys.view(np.uint32)
+        payload = rng.integers(1, 1 << 23, size=nan_count, dtype=np.uint32)
+        sign = rng.integers(0, 2, size=nan_count, dtype=np.uint32) << np.uint32(31)
+        bits[where] = np.uint32(0x7F800000) | payload | sign
+        vals = rng.permutation(n).astype(np.uint32)
+        check_against_oracle(sq, keys, vals, "f32", seed=nan_count, cutoff=65536)
+        if n > 2048:  # also as a recursion whose leaves carry a few NaNs each
+            check_against_oracle(sq, keys, vals, "f32", seed=nan_count, cutoff=2048)
