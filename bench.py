@@ -283,6 +283,129 @@ def bench_plain(args, sq, dist, rank, world, local):
     return out
 
 
+def check_sorted_any(src_bits, keys_bits, vals, dtype) -> bool:
+    """Device check for any key type: non-decreasing (ordinal(key), val), vals a
+    permutation, every key's bits equal to the original key at its payload
+    index -- together these pin the unique sorted result."""
+    import torch
+
+    n = keys_bits.numel()
+    v = vals.to(torch.int64) & 0xFFFFFFFF
+    if dtype == "u64":
+        o = keys_bits ^ torch.tensor(-(1 << 63), dtype=torch.int64, device=keys_bits.device)
+    else:
+        b = keys_bits.to(torch.int64) & 0xFFFFFFFF
+        if dtype == "f32":
+            nan = (b & 0x7FFFFFFF) > 0x7F800000
+            neg = (b & 0x80000000) != 0
+            b = torch.where(nan, torch.full_like(b, 0xFFFFFFFF), torch.where(neg, b ^ 0xFFFFFFFF, b | 0x80000000))
+        o = b
+    ok = bool(((o[1:] > o[:-1]) | ((o[1:] == o[:-1]) & (v[1:] > v[:-1]))).all())
+    seen = torch.zeros(n, dtype=torch.bool, device=vals.device)
+    seen[v] = True
+    return ok and bool(seen.all()) and bool((src_bits[v] == keys_bits).all())
+
+
+def bench_wide(args, sq, dist, rank, world, local):
+    """Wide keys: n uint64 keys, Zipf(1.1) ranks over [1, 2^40] through a seeded
+    bijection, and n float32 keys N(0,1) with 0.1% +-inf, 0.1% -0.0 and 0.01%
+    NaN, index payload; one step sorts one array of each."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2407_14801_gb300 import dist as D
+
+    dev = torch.device("cuda", local)
+    n = args.wide_n
+    src = {"u64": torch.from_numpy(W.zipf_u64(n, 31).view(np.int64)).to(dev),
+           "f32": torch.from_numpy(W.normal_f32(n, 32)).to(dev)}
+    iota = torch.arange(n, dtype=torch.int32, device=dev)
+    total = args.warmup + args.steps
+    bufs = [{d: (src[d].clone(), iota.clone()) for d in src} for _ in range(total)]
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        for d in ("u64", "f32"):
+            k, v = bufs[i][d]
+            sq.sort(k, v, seed=i, dtype=d, cutoff=args.cutoff)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    sq.reset_stats()
+    sq.set_profiling(True)
+    vis = [x for x in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if x.strip()]
+    clocks = ClockSampler(int(vis[local]) if local < len(vis) and vis[local].strip().isdigit() else local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    D.barrier(dist)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for i in range(args.warmup, total):
+        step(i)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    D.barrier(dist)
+    clk = clocks.stop()
+    sq.set_profiling(False)
+    st = sq.stats()
+    ms_max = D.max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
+    value = world * args.steps * 2 * n / (ms_max / 1e3) / 1e9
+    bits = {"u64": lambda t: t, "f32": lambda t: t.view(torch.int32)}
+    ok = all(check_sorted_any(bits[d](src[d]), bits[d](bufs[i][d][0]), bufs[i][d][1], d)
+             for i in range(args.warmup, total) for d in src)
+    del bufs
+    torch.cuda.empty_cache()
+    fams = [f for f in st["ms"] if st["launches"][f] > 0 and st["bytes"][f] > 0]
+    dom = max(fams, key=lambda f: st["ms"][f])
+    L = st["launches"][dom]
+    bytes_per_launch = st["bytes"][dom] / L
+    avg_ms = st["ms"][dom] / L
+    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    peak, peak_src = measured_peaks()
+    workload_name = f"wide_u64_f32_n{n}"
+    roofline = {"bound": "hbm", "kernel": f"k_{dom}", "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": profiled_traffic(dom, workload_name),
+                "peak_source": f"{peak_src} (copy bandwidth)", "algorithmic_bytes_per_launch": bytes_per_launch,
+                "avg_launch_ms": avg_ms, "launches": L,
+                "family_ms": {f: round(st["ms"][f], 3) for f in st["ms"] if st["launches"][f]}}
+    step_frac = (6 * (12 + 8) * n) / (ms_max / args.steps / 1e3) / 1e9 / peak
+    e2e = None
+    if not args.no_e2e:
+        hosts = {d: src[d].cpu() for d in src}
+        pins = {d: torch.empty_like(hosts[d]).pin_memory() for d in src}
+        hv = torch.empty(n, dtype=torch.int32).pin_memory()
+        iota_h = torch.arange(n, dtype=torch.int32)
+        tot, reps = 0.0, min(args.steps, 2)
+        for i in range(reps):
+            for d in src:
+                pins[d].copy_(hosts[d])
+                hv.copy_(iota_h)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                sq.sort(pins[d], hv, seed=100 + i, dtype=d)
+                tot += time.perf_counter() - t0
+        e2e = {"value": round(reps * 2 * n / tot / 1e9, 3), "unit": UNIT,
+               "h2d_bytes_per_step": (12 + 8) * n, "d2h_bytes_per_step": (12 + 8) * n, "steps": reps,
+               "buffers": "pinned host"}
+    return {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64+f32", "data": "synthetic",
+        "config": {"workload": workload_name, "n_per_array": n, "keys": ["uint64 Zipf(1.1) over 2^40 ranks, bijection",
+                                                                            "float32 N(0,1) + 0.1% inf, 0.1% -0, 0.01% NaN"],
+                   "payload": "uint32 original index", "seeds": {"u64": 31, "f32": 32},
+                   "step": "one uint64 sort and one float32 sort", "cutoff": args.cutoff or "tuned table",
+                   "l2": "inputs larger than L2 (each step sorts its own copies)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline, "step_hbm_frac_ideal_6wn": round(step_frac, 4), "e2e": e2e,
+        "gpu_launches": int(sum(st["launches"].values())),
+        "rounds_per_step": st["rounds"] / max(1, args.steps), "clocks": clk, "verified": ok,
+    }
+
+
 def bench_e2e(sq, n, steps, dev, inputs):
     import torch
 
@@ -330,6 +453,27 @@ def cpu_baseline(sample_log2: int = 23, budget_s: float = 25.0):
                       f"cutoff 16384, single thread", "seconds": round(t, 2)}
 
 
+def cpu_baseline_wide(sample_log2: int = 21, budget_s: float = 20.0):
+    """The CPU oracle, single-threaded, on the first 2^sample_log2 keys of the
+    wide workload's two generators."""
+    import oracle
+    import workloads as W
+
+    n = 1 << sample_log2
+    done, t = 0, 0.0
+    for dt, gen in (("u64", lambda: W.zipf_u64(n, 31)), ("f32", lambda: W.normal_f32(n, 32))):
+        k = gen()
+        t0 = time.perf_counter()
+        oracle.sort(k, W.iota(n), seed=1, cutoff=16384, dtype=dt)
+        t += time.perf_counter() - t0
+        done += n
+        if t > budget_s:
+            break
+    return {"value": round(done / t / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"2^{sample_log2} uint64 Zipf keys and 2^{sample_log2} float32 keys (first keys of the "
+                      f"workload's generators), cutoff 16384, single thread", "seconds": round(t, 2)}
+
+
 def run_ours(args):
     import torch
 
@@ -341,10 +485,15 @@ def run_ours(args):
     import paper_2407_14801_gb300 as sq
 
     sq.lib()
+    sq.set_launch_mode(args.launch_mode)
     if args.workload == "plain":
         out = bench_plain(args, sq, dist, rank, world, local)
         if rank == 0 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline()
+    elif args.workload == "wide":
+        out = bench_wide(args, sq, dist, rank, world, local)
+        if rank == 0 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline_wide()
     elif args.workload == "batch":
         out = bench_batch(args, sq, dist, rank, world, local)
     elif args.workload == "serve":
@@ -371,7 +520,7 @@ def bench_batch(args, sq, dist, rank, world, local):
 
     dev = torch.device("cuda", local)
     count = args.batch_count
-    sizes = W.batch_sizes(count, 7)
+    sizes = W.batch_sizes(count, 7, args.batch_lo, args.batch_hi)
     mine = list(D.shard(count, rank, world))
     src = [torch.from_numpy(W.uniform_u32(int(sizes[i]), (7 << 20) + i + 1).view(np.int32)).to(dev) for i in mine]
     keys = [t.clone() for t in src]
@@ -411,22 +560,24 @@ def bench_batch(args, sq, dist, rank, world, local):
     sq.reset_stats()
     ms_b = timed(run_batched, args.steps, args.warmup)
     st = sq.stats()
-    ms_s = timed(run_single, max(1, args.steps // 4), 1)
+    ms_s = None if args.batch_no_single else timed(run_single, max(1, args.steps // 4), 1)
     # correctness of the last batched step is checked instance by instance
     restore()
     run_batched()
     ok = all(check_sorted_u32(k, v, s0) for k, v, s0 in zip(keys, vals, src))
     all_keys = int(sizes.sum())
     gk_b = world * total_keys / (ms_b / 1e3) / 1e9
-    gk_s = world * total_keys / (ms_s / 1e3) / 1e9
+    gk_s = world * total_keys / (ms_s / 1e3) / 1e9 if ms_s else None
     return {"metric": METRIC, "value": round(gk_b, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_b, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": f"batch_u32_{count}_instances_2^8..2^20", "instances": count,
+            "config": {"workload": f"batch_u32_{count}_instances_2^{args.batch_lo}..2^{args.batch_hi}",
+                       "instances": count,
                        "total_keys": all_keys, "seed": 7, "cutoff": sq.get_cutoff("u32"),
                        "parallelism": f"instances sharded over {world} rank(s)"},
-            "per_instance_launches": {"value": round(gk_s, 3), "unit": UNIT, "ms_per_step": round(ms_s, 3)},
-            "batched_over_per_instance": round(ms_s / ms_b, 2),
+            "per_instance_launches": ({"value": round(gk_s, 3), "unit": UNIT, "ms_per_step": round(ms_s, 3)}
+                                      if ms_s else None),
+            "batched_over_per_instance": round(ms_s / ms_b, 2) if ms_s else None,
             "gpu_launches_per_step": sum(st["launches"].values()) / max(1, args.steps + args.warmup),
             "rounds_per_step": st["rounds"] / max(1, args.steps + args.warmup), "verified": ok}
 
@@ -533,12 +684,19 @@ def main():
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="plain", choices=["plain", "batch", "serve"])
+    ap.add_argument("--workload", default="plain", choices=["plain", "wide", "batch", "serve"])
     ap.add_argument("--n", type=int, default=1 << 28)
     ap.add_argument("--cutoff", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--batch-lo", type=int, default=8, help="log2 of the smallest batch instance")
+    ap.add_argument("--batch-hi", type=int, default=20, help="log2 of the largest batch instance")
+    ap.add_argument("--batch-no-single", action="store_true",
+                    help="skip the per-instance comparison (profiling runs)")
+    ap.add_argument("--wide-n", type=int, default=1 << 26, help="keys per array of the wide workload")
+    ap.add_argument("--launch-mode", default="auto", choices=["auto", "host", "graph"],
+                    help="how recursion rounds are launched (profilers cannot see kernels inside graph loops)")
     ap.add_argument("--dists", default=",".join(DISTS), help="comma-separated subset (profiling runs)")
     ap.add_argument("--serve-requests", type=int, default=512)
     args = ap.parse_args()

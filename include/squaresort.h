@@ -215,8 +215,9 @@ uint32_t sq_cutoff_for(sq_dtype dtype, uint64_t n);
  *                   loop ends when every instance is sorted; kernels read
  *                   their work counts on the device.  The graph is built once
  *                   per thread and device and reused by later calls.
- *  SQ_LAUNCH_AUTO : (default) the graph for sq_sort_batch and the server,
- *                   host rounds for sq_sort / sq_sort_ex.
+ *  SQ_LAUNCH_AUTO : (default) currently host rounds everywhere: the graph
+ *                   launches every step of a round at a fixed size and was
+ *                   measured slower for single, batched and served sorts.
  * Results do not depend on the mode.  While profiling is on
  * (sq_set_profiling) rounds are always host-launched, so that every kernel
  * is timed. */

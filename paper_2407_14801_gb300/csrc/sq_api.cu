@@ -38,10 +38,9 @@ uint32_t default_cutoff(sq_dtype d) {
 // How recursion rounds are launched (sq_set_launch_mode).
 std::atomic<int> g_launch_mode{SQ_LAUNCH_AUTO};
 
-int graph_for(bool many) {
-  const int m = g_launch_mode.load();
-  return m == SQ_LAUNCH_GRAPH || (m == SQ_LAUNCH_AUTO && many) ? 1 : 0;
-}
+// SQ_LAUNCH_AUTO runs host rounds: graph rounds launch every step of a
+// round at a fixed size and measured slower on every workload here.
+int graph_for(bool) { return g_launch_mode.load() == SQ_LAUNCH_GRAPH ? 1 : 0; }
 
 // A cutoff set with sq_set_cutoff wins; else the tuned table's entry for
 // floor(log2 n); else the largest leaf.
@@ -112,7 +111,9 @@ sq_status sort_device(void *keys, uint32_t *vals, uint64_t n, sq_dtype dtype, ui
   keep_pool_cached();
   DevBuf scratch, iota;
   scratch.st = iota.st = st;
-  cudaError_t e = cudaMallocAsync(&scratch.p, std::max<size_t>(n, 1) * (w + 4) + 256, st);
+  const size_t dk_bytes = (std::max<size_t>(n, 1) * w + 255) & ~(size_t)255;
+  const size_t dv_bytes = (std::max<size_t>(n, 1) * 4 + 255) & ~(size_t)255;
+  cudaError_t e = cudaMallocAsync(&scratch.p, dk_bytes + dv_bytes + std::max<size_t>(n, 1), st);
   if (e != cudaSuccess) return fail(SQ_ERR_NOMEM, "scratch allocation of %llu elements failed: %s",
                                     (unsigned long long)n, cudaGetErrorString(e));
   uint32_t *v = vals;
@@ -126,7 +127,8 @@ sq_status sort_device(void *keys, uint32_t *vals, uint64_t n, sq_dtype dtype, ui
   is.keys = keys;
   is.vals = v;
   is.dkeys = scratch.p;
-  is.dvals = (uint32_t *)((char *)scratch.p + ((std::max<size_t>(n, 1) * w + 255) & ~(size_t)255));
+  is.dvals = (uint32_t *)((char *)scratch.p + dk_bytes);
+  is.tags = (uint8_t *)scratch.p + dk_bytes + dv_bytes;
   is.n = n;
   is.seed = seed;
   sq::RunSpec spec;
@@ -285,6 +287,12 @@ sq_status sq_skew_transpose(const sq_skew_buf *buf, uint64_t rows, uint64_t cols
   is.dvals = const_cast<uint32_t *>(buf->vals_in);
   is.n = n;
   is.seed = 0;
+  DevBuf tags;  // the count's bucket of every element, read by the SkewTranspose
+  tags.st = (cudaStream_t)stream;
+  keep_pool_cached();
+  if (cudaMallocAsync(&tags.p, std::max<uint64_t>(n, 1), (cudaStream_t)stream) != cudaSuccess)
+    return fail(SQ_ERR_NOMEM, "tag scratch of %llu bytes", (unsigned long long)n);
+  is.tags = (uint8_t *)tags.p;
   sq::RunSpec spec;
   memset(&spec, 0, sizeof(spec));
   spec.inst = &is;
@@ -333,11 +341,13 @@ sq_status sq_sort_batch(const sq_sort_desc *descs, uint32_t count, sq_stream_t s
       off += (b + 255) & ~(size_t)255;
       return o;
     };
+    std::vector<size_t> toff(ids.size());
     for (size_t q = 0; q < ids.size(); q++) {
       const uint64_t n = descs[ids[q]].n;
       koff[q] = carve(n * w);
       voff[q] = carve(n * 4);
       ioff[q] = descs[ids[q]].vals ? 0 : carve(n * 4);
+      toff[q] = carve(n);
     }
     DevBuf slab;
     slab.st = st;
@@ -356,6 +366,7 @@ sq_status sq_sort_batch(const sq_sort_desc *descs, uint32_t count, sq_stream_t s
       }
       is[q].dkeys = (char *)slab.p + koff[q];
       is[q].dvals = (uint32_t *)((char *)slab.p + voff[q]);
+      is[q].tags = (uint8_t *)slab.p + toff[q];
       is[q].n = ds.n;
       is[q].seed = ds.seed;
       is[q].cutoff = cutoff_for((sq_dtype)d, ds.n);

@@ -178,8 +178,12 @@ struct Engine {
       case 2: return launch_leaf<128, 16, false>(L, cp, 2, count, nsm);
       case 3: return launch_leaf<512, 16, false>(L, cp, 3, count, nsm);
       case 4: return launch_leaf_cluster<512, 16, 2>(L, cp, 4, count, nsm);
-      case 5: return launch_leaf_cluster<512, 16, 4>(L, cp, 5, count, nsm);
-      default: return launch_leaf_cluster<512, 16, 8>(L, cp, 6, count, nsm);
+      case 5: return launch_leaf_cluster<512, 16, 3>(L, cp, 5, count, nsm);
+      case 6: return launch_leaf_cluster<512, 16, 4>(L, cp, 6, count, nsm);
+      case 7: return launch_leaf_cluster<512, 16, 5>(L, cp, 7, count, nsm);
+      case 8: return launch_leaf_cluster<512, 16, 6>(L, cp, 8, count, nsm);
+      case 9: return launch_leaf_cluster<512, 16, 7>(L, cp, 9, count, nsm);
+      default: return launch_leaf_cluster<512, 16, 8>(L, cp, 10, count, nsm);
     }
   }
 
@@ -237,6 +241,7 @@ struct Engine {
     u64 *bucket_start;
     u64 k;
     double skew_elems;  // skew_only: elements moved
+    int tags;           // every instance has tag scratch
   };
 
   static cudaError_t issue_round(Launcher &L, const Ctx *cp, const Counters *hc, const RoundArgs &A) {
@@ -295,9 +300,14 @@ struct Engine {
       L.end();
       SQ_TRY(cudaGetLastError());
       const size_t smem_skew = sizeof(SkewSmem<DT, SKEW_CAP>);
-      SQ_TRY(set_smem(k_skew<DT, SKEW_CAP>, smem_skew));
       L.begin(KF_SKEW);
-      k_skew<DT, SKEW_CAP><<<grid_skew, 256, smem_skew, st>>>(cp, ready);
+      if (A.tags) {  // every instance has tag scratch: the count's buckets are reused
+        SQ_TRY(set_smem(k_skew<DT, SKEW_CAP, true>, smem_skew));
+        k_skew<DT, SKEW_CAP, true><<<grid_skew, 256, smem_skew, st>>>(cp, ready);
+      } else {
+        SQ_TRY(set_smem(k_skew<DT, SKEW_CAP, false>, smem_skew));
+        k_skew<DT, SKEW_CAP, false><<<grid_skew, 256, smem_skew, st>>>(cp, ready);
+      }
       L.end();
       L.local.bytes[KF_SKEW] += 2.0 * (KEY_BYTES + 4) * re;
       SQ_TRY(cudaGetLastError());
@@ -406,6 +416,7 @@ struct Engine {
     RoundArgs A;
     memset(&A, 0, sizeof(A));
     A.nsm = nsm;
+    A.tags = 1;  // graph runs are sorts whose instances all carry tag scratch
     // first round of the body, then the conditional second round
     SQ_CU(cudaStreamBeginCaptureToGraph(G.cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     cudaError_t ce = issue_round(L, G.ctx, nullptr, A);
@@ -661,6 +672,7 @@ struct Engine {
       hinst[i].vals = is.vals;
       hinst[i].dkeys = is.dkeys;
       hinst[i].dvals = is.dvals;
+      hinst[i].tags = is.tags;
       hinst[i].n = is.n;
       hinst[i].cutoff = cutoff_of(i);
       hinst[i].pad = 0;
@@ -761,6 +773,8 @@ struct Engine {
     A.bucket_start = (u64 *)spec.bucket_start;
     A.k = spec.k;
     A.skew_elems = spec.skew_only ? (double)spec.inst[0].n : 0.0;
+    A.tags = 1;
+    for (u32 i = 0; i < ninst; i++) A.tags &= spec.inst[i].tags != nullptr;
     u32 done = hs.done;
     int rc = 0;
     u64 rounds = 0;
@@ -788,7 +802,7 @@ struct Engine {
                S.error);
       return (S.error & ERRB_ATTEMPTS) ? 7 : ((S.error & ERRB_SIZES) ? 8 : 2);
     };
-    const bool graph = spec.graph && !spec.skew_only && !L.prof && done < ninst;
+    const bool graph = spec.graph && !spec.skew_only && A.tags && !L.prof && done < ninst;
     if (graph) {
       // ---- every round on the device: one graph launch (relaunched only
       // after the host has grown the node pool)

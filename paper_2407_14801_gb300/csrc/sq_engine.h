@@ -35,6 +35,7 @@ struct InstSpec {
   uint32_t *vals;  // A vals (device)
   void *dkeys;     // D keys scratch (device), same length
   uint32_t *dvals; // D vals scratch (device)
+  uint8_t *tags;   // n bytes of scratch (device) for bucket tags; NULL: the SkewTranspose classifies
   uint64_t n;
   uint64_t seed;
   uint32_t cutoff;  // 0: RunSpec::cutoff

@@ -26,34 +26,37 @@ namespace sq {
 template <int DT>
 struct LeafCfg;
 // Leaf classes (elements per class): c0 = warp x 2 (64), c1 = warp x 16
-// (512), c2 = 128 x 16 (2048), c3 = 512 x 16 (8192), c4 = 16384, c5 = 32768,
-// c6 = 65536.  All are merge sorts: c0..c3 on one warp or one CTA, c4..c6 on
-// clusters of 2, 4 and 8 CTAs of 512 x 16 whose cross-CTA rounds copy each
-// CTA's merge window out of the others' shared memory.  Pivot samples use
-// the single-CTA sorters only.
+// (512), c2 = 128 x 16 (2048), c3 = 512 x 16 (8192), and c4..c10 = clusters
+// of g = 2..8 CTAs of 512 x 16 (g * 8192 elements: a leaf takes the
+// smallest cluster that holds it).  All are merge sorts; the cluster rounds
+// copy each CTA's merge window out of the others' shared memory.  Pivot
+// samples use the single-CTA sorters only.
+template <int DT>
+struct LeafCfg;
 template <>
 struct LeafCfg<DT_U32> {
-  static constexpr int nclass = 7;
+  static constexpr int nclass = kLeafClasses;
   static constexpr u32 max_pivots = 16384;
 };
 template <>
 struct LeafCfg<DT_F32> {
-  static constexpr int nclass = 7;
+  static constexpr int nclass = kLeafClasses;
   static constexpr u32 max_pivots = 8192;
 };
 template <>
 struct LeafCfg<DT_U64> {
-  static constexpr int nclass = 7;
+  static constexpr int nclass = kLeafClasses;
   static constexpr u32 max_pivots = 8192;
 };
+constexpr u32 kClusterPart = 8192;  // elements per CTA of the cluster classes
 __host__ __device__ __forceinline__ u32 class_cap(int c) {
-  return c == 0 ? 64u : c == 1 ? 512u : c == 2 ? 2048u : c == 3 ? 8192u : c == 4 ? 16384u : c == 5 ? 32768u : 65536u;
+  return c == 0 ? 64u : c == 1 ? 512u : c == 2 ? 2048u : (u32)(c - 2) * kClusterPart;
 }
 
 __host__ __device__ __forceinline__ int class_of(u32 n, int nclass) {
-  int c = 0;
-  while (c < nclass - 1 && n > class_cap(c)) ++c;
-  return c;
+  if (n <= 2048) return n <= 64 ? 0 : n <= 512 ? 1 : 2;
+  const int c = 2 + (int)((n + kClusterPart - 1) / kClusterPart);
+  return c < nclass ? c : nclass - 1;
 }
 
 // number of pivots <= e in piv[lo, hi)
@@ -681,6 +684,7 @@ __global__ void __launch_bounds__(1024) k_count(const Ctx *__restrict__ cp, u32 
     const Inst I = c.inst[nd.inst];
     const key_t *dk = (const key_t *)I.dkeys + nd.off;
     const u32 *dv = I.dvals + nd.off;
+    uint8_t *tg = I.tags ? I.tags + nd.off : nullptr;
     u32 *P = meta + ML.P;
     const u32 rows = nd.rows, n = nd.n, cols = nd.cols, nkb = nd.nkb;
     const u32 Iblk = u - nd.unit_base;
@@ -726,6 +730,7 @@ __global__ void __launch_bounds__(1024) k_count(const Ctx *__restrict__ cp, u32 
         } else {
           b = upper_bound_e<K>(piv, 0, np, e);
         }
+        if (tg && valid) tg[p] = (uint8_t)(b & (kSkewBkts - 1));  // for the SkewTranspose
         // bucket totals: one atomic per run of equal buckets
         const int prevb = __shfl_up_sync(0xffffffffu, b, 1);
         const bool start = valid && (lane == 0 || prevb != b);
@@ -879,7 +884,7 @@ __device__ __forceinline__ u32 warp_excl_scan(u32 v, u32 &total) {
   return inc - v;
 }
 
-template <int DT, int CAP>
+template <int DT, int CAP, bool TAGS>
 __global__ void __launch_bounds__(256) k_skew(const Ctx *__restrict__ cp, u32 ready_count) {
   const Ctx &c = *cp;
   if (ready_count == kDev) ready_count = min(c.cnt_cur->ready, c.ready_cap);
@@ -942,6 +947,7 @@ __global__ void __launch_bounds__(256) k_skew(const Ctx *__restrict__ cp, u32 re
     const Inst I = c.inst[nd.inst];
     const key_t *dk = (const key_t *)I.dkeys + nd.off;
     const u32 *dv = I.dvals + nd.off;
+    const uint8_t *tg = TAGS ? I.tags + nd.off : nullptr;
     key_t *ak = (key_t *)I.keys + nd.off;
     u32 *av = I.vals + nd.off;
     const int npiv = (int)nk - 1;
@@ -983,15 +989,20 @@ __global__ void __launch_bounds__(256) k_skew(const Ctx *__restrict__ cp, u32 re
           const bool valid = q < pe;
           const u32 vmask = __ballot_sync(0xffffffffu, valid);
           const int lastv = 31 - __clz(vmask);
-          E e = K::top();
-          if (valid) {
-            const u32 p = sm.seg_start[ci] + (q - sm.seg_pre[ci]);
-            e = K::make(dk[p], dv[p]);
+          int jb;
+          if constexpr (TAGS) {  // the count recorded every element's bucket
+            jb = valid ? (int)tg[sm.seg_start[ci] + (q - sm.seg_pre[ci])] : 0;
+          } else {
+            E e = K::top();
+            if (valid) {
+              const u32 p = sm.seg_start[ci] + (q - sm.seg_pre[ci]);
+              e = K::make(dk[p], dv[p]);
+            }
+            const int lo = carry_b < 0 ? 0 : carry_b;
+            const E elast = shfl_e(e, lastv);
+            const int hi = warp_bucket_from<K>(sm.piv, lo, npiv, elast);
+            jb = valid ? upper_bound_e<K>(sm.piv, lo, hi, e) : hi;
           }
-          const int lo = carry_b < 0 ? 0 : carry_b;
-          const E elast = shfl_e(e, lastv);
-          const int hi = warp_bucket_from<K>(sm.piv, lo, npiv, elast);
-          const int jb = valid ? upper_bound_e<K>(sm.piv, lo, hi, e) : hi;
           const int prevb = __shfl_up_sync(0xffffffffu, jb, 1);
           const int nextb = __shfl_down_sync(0xffffffffu, jb, 1);
           if (valid) {

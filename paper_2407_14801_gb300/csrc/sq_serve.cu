@@ -51,7 +51,7 @@ struct Req {
 
 uint64_t data_bytes(const sq_sort_desc &d) {
   const uint64_t n = d.n, w = kbytes(d.dtype);
-  return al(n * w) + al(n * 4) + al(n * w) + al(n * 4) + 256;
+  return al(n * w) + al(n * 4) + al(n * w) + al(n * 4) + al(n) + 256;
 }
 
 }  // namespace
@@ -135,6 +135,7 @@ void run_batch(sq_server *s, cudaStream_t st, std::vector<Req *> &batch, uint64_
       x.vals = (uint32_t *)(base + al(n * w));
       x.dkeys = base + al(n * w) + al(n * 4);
       x.dvals = (uint32_t *)(base + al(n * w) + al(n * 4) + al(n * w));
+      x.tags = (uint8_t *)(base + al(n * w) + al(n * 4) + al(n * w) + al(n * 4));
       x.n = n;
       x.seed = r->d.seed;
       x.cutoff = s->cutoff ? s->cutoff : sq_cutoff_for((sq_dtype)d, n);
@@ -156,7 +157,7 @@ void run_batch(sq_server *s, cudaStream_t st, std::vector<Req *> &batch, uint64_
     spec.inst = is.data();
     spec.ninst = (uint32_t)is.size();
     spec.cutoff = s->cutoff ? s->cutoff : sq_get_cutoff((sq_dtype)d);
-    spec.graph = sq_get_launch_mode() != SQ_LAUNCH_HOST;
+    spec.graph = sq_get_launch_mode() == SQ_LAUNCH_GRAPH;
     spec.dev_alloc = bump_alloc;
     spec.dev_free = bump_free;
     spec.alloc_ctx = &bump;

@@ -211,11 +211,11 @@ struct Sorter {
   }
 };
 
-// A leaf of up to G*T*R elements sorted by a cluster of G CTAs: each CTA
-// sorts its T*R elements with Sorter, then log2(G) merge rounds run across
-// the cluster, every thread reading the two runs it merges from whichever
-// CTAs' shared memory holds them (distributed shared memory).  Outputs go
-// through registers between rounds, as in the in-CTA rounds.
+// A leaf of up to G*T*R elements sorted by a cluster of G CTAs (any G up
+// to 8): each CTA sorts its T*R elements with Sorter, then ceil(log2 G)
+// merge rounds run across the cluster on runs held in the CTAs' shared
+// memories (distributed shared memory).  Outputs go through registers
+// between rounds, as in the in-CTA rounds.
 template <class K, int T, int R, int G>
 struct ClusterSorter {
   typedef Sorter<K, T, R, false> S;
@@ -251,7 +251,13 @@ struct ClusterSorter {
     auto at = [&](int gi) -> E { return *cl.map_shared_rank(s + S::px(gi % NC), gi / NC); };
 #pragma unroll 1
     for (int w = NC; w < N; w <<= 1) {
-      if (idle) {  // the same barriers as the others, nothing else
+      const int p0 = rank * NC;
+      const int base = p0 & ~(2 * w - 1);
+      const int bb = base + w;
+      // runs of this round's pair: A = [base, base + wa), B = [bb, bb + wb)
+      // (with G not a power of two the last pair may be short or single)
+      const int wa = min(w, N - base), wb = max(0, min(w, N - bb));
+      if (idle || wb == 0) {  // nothing to merge: the same barriers as the others
         cl.sync();
         __syncthreads();
         cl.sync();
@@ -262,14 +268,11 @@ struct ClusterSorter {
 #pragma unroll
       for (int k = 0; k < R; k++) s[S::px(tid * R + k)] = x[k];
       cl.sync();
-      const int p0 = rank * NC;
-      const int base = p0 & ~(2 * w - 1);
-      const int bb = base + w;
       if (warp < 2) {
         // smallest i in [lo, hi] with B[d-1-i] < A[i] (hi if none): i elements
         // of the first d outputs come from A
         const int d = p0 - base + warp * NC;
-        int lo = d > w ? d - w : 0, hi = d < w ? d : w;
+        int lo = d > wb ? d - wb : 0, hi = d < wa ? d : wa;
         while (hi - lo > 32) {
           const int step = (hi - lo + 31) / 32;
           const int q = lo + lane * step;

@@ -25,7 +25,7 @@ enum : u32 {
 
 constexpr u32 kNone = 0xffffffffu;
 constexpr int kMaxAttempts = 256;  // pivot samples per node before giving up
-constexpr int kLeafClasses = 7;
+constexpr int kLeafClasses = 11;
 
 // Child kinds (Algorithm 1): the root, a column sort, a bucket sort.
 enum : u32 { KIND_ROOT = 0, KIND_COL = 1, KIND_BUC = 2 };
@@ -200,6 +200,7 @@ struct Inst {
   u32 *vals;   // A vals
   void *dkeys; // D keys (scratch)
   u32 *dvals;  // D vals (scratch)
+  uint8_t *tags;  // per element of D: its bucket within its 64-bucket block (written by the count)
   u64 n;
   u32 cutoff;  // leaf iff a node's n <= cutoff (per instance)
   u32 pad;

@@ -65,7 +65,7 @@ def check_against_oracle(sq, keys, vals, dtype, seed, cutoff):
 
 
 SIZES = [1, 2, 3, 4, 16, 17, 63, 64, 65, 100, 511, 512, 513, 1000, 2048, 2049, 5000, 8192, 8193, 16384, 16385,
-         32768, 32769, 40000, 65536, 65537, 200003, 1000003]
+         24576, 24577, 32768, 32769, 40000, 45000, 50000, 57344, 57345, 65536, 65537, 200003, 1000003]
 
 
 @pytest.mark.parametrize("cutoff", [2, 3, 16, 64, 512, 2048, 8192, 16384, 32768, 65536])
@@ -170,7 +170,7 @@ def test_empty_and_tiny(sq):
         assert (gk == np.sort(keys)).all()
 
 
-@pytest.mark.parametrize("n", [60, 500, 2000, 8000, 16000, 30000, 65536])
+@pytest.mark.parametrize("n", [60, 500, 2000, 8000, 16000, 20000, 30000, 40000, 45000, 52000, 65536])
 def test_f32_leaf_nan_bits_restored(sq, n):
     """Single-leaf float32 sorts with 0, 1, a few, exactly 64, 65 and many NaNs
     of random sign and payload: the leaf kernels hold float keys as one
