@@ -44,7 +44,7 @@ struct Engine {
   static constexpr int LDT = DT == DT_F32 ? DT_F32W : DT;
   typedef KT<LDT> KL;
   typedef typename KL::elem_t EL;
-  static constexpr bool kFix = KL::lossy;  // leaves may go to the fix list
+  static constexpr bool kFix = KL::lossy;  // NaN-heavy float32 leaves go to the fix list
   static constexpr u32 kHostExpandCols = 2048;  // roots with this many columns are expanded on the host
 
   static u32 max_leaf() { return class_cap(NCLASS - 1); }
@@ -125,8 +125,7 @@ struct Engine {
 
   template <int T, int R, bool WARP>
   static cudaError_t launch_leaf(Launcher &L, const Ctx *cp, int cls, u32 count, int nsm) {
-    typedef Sorter<KL, T, R, WARP> S;
-    const size_t smem = (size_t)(WARP ? 8 : 1) * (S::SMEM * sizeof(EL) + (KL::lossy ? 4 * kNanWords : 0));
+    const size_t smem = leaf_sort_bytes<LDT, T, R, WARP>() + (KL::lossy ? (WARP ? 8 : 1) * 4 * kNanWords : 0);
     auto kern = k_leaf<LDT, T, R, WARP>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
@@ -160,7 +159,7 @@ struct Engine {
 
   template <int T, int R, int G>
   static cudaError_t launch_leaf_cluster(Launcher &L, const Ctx *cp, int cls, u32 count, int nsm) {
-    const size_t smem = sizeof(EL) * (size_t)Sorter<KL, T, R, false>::SMEM + (KL::lossy ? 4 * kNanWords : 0);
+    const size_t smem = leaf_sort_bytes<LDT, T, R, false>() + (KL::lossy ? 4 * kNanWords : 0);
     auto kern = k_leaf_cluster<LDT, T, R, G>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
@@ -242,12 +241,14 @@ struct Engine {
     u64 k;
     double skew_elems;  // skew_only: elements moved
     int tags;           // every instance has tag scratch
+    u32 kmax;           // graph rounds: the largest k of any node of the run
   };
 
   static cudaError_t issue_round(Launcher &L, const Ctx *cp, const Counters *hc, const RoundArgs &A) {
     const cudaStream_t st = L.st;
     const int nsm = A.nsm;
-    const int grid_count = nsm * 2, grid_scan = nsm * 8, grid_skew = nsm * 5, grid_expand = nsm * 4;
+    const int grid_count = nsm * 2, grid_scan = nsm * 8, grid_skew = nsm * 5, grid_skew_tags = nsm * 4,
+              grid_expand = nsm * 4;
     cudaError_t e;
 #define SQ_TRY(x)                      \
   do {                                 \
@@ -274,7 +275,7 @@ struct Engine {
       k_plan<<<1, 1024, 0, st>>>(cp, ready, K::key_words);
       L.end();
       SQ_TRY(cudaGetLastError());
-      const u32 kmax = hc ? std::max<u32>(hc->max_ready_k, 2) : max_pivots() + 1;
+      const u32 kmax = hc ? std::max<u32>(hc->max_ready_k, 2) : A.kmax;
       if (A.skew_only) {
         L.begin(KF_AUX);
         k_put_pivots<DT><<<((u32)A.k + 255) / 256, 256, 0, st>>>(cp, (const typename K::key_t *)A.piv_keys,
@@ -301,9 +302,10 @@ struct Engine {
       SQ_TRY(cudaGetLastError());
       const size_t smem_skew = sizeof(SkewSmem<DT, SKEW_CAP>);
       L.begin(KF_SKEW);
-      if (A.tags) {  // every instance has tag scratch: the count's buckets are reused
-        SQ_TRY(set_smem(k_skew<DT, SKEW_CAP, true>, smem_skew));
-        k_skew<DT, SKEW_CAP, true><<<grid_skew, 256, smem_skew, st>>>(cp, ready);
+      if (A.tags) {  // every instance has tag scratch: a counting sort by the count's tags
+        const size_t smem_tags = sizeof(SkewTagSmem<DT, SKEW_CAP>);
+        SQ_TRY(set_smem(k_skew_tags<DT, SKEW_CAP>, smem_tags));
+        k_skew_tags<DT, SKEW_CAP><<<grid_skew_tags, 256, smem_tags, st>>>(cp, ready);
       } else {
         SQ_TRY(set_smem(k_skew<DT, SKEW_CAP, false>, smem_skew));
         k_skew<DT, SKEW_CAP, false><<<grid_skew, 256, smem_skew, st>>>(cp, ready);
@@ -384,15 +386,17 @@ struct Engine {
     }
     ~GraphSlot() { reset(); }
   };
-  static GraphSlot &graph_slot() {
-    static thread_local GraphSlot s;
-    return s;
+  // One graph per bound on the nodes' k (a power of two, so that the count
+  // kernel's shared memory and the pivot-sort launches fit the run).
+  static GraphSlot &graph_slot(int kb) {
+    static thread_local GraphSlot s[16];
+    return s[kb];
   }
 
   static constexpr unsigned long long kMaxRounds = 4096;  // far above any recursion depth
 
   // Builds (once per thread, device and instance count) the graph of rounds.
-  static int graph_prepare(GraphSlot &G, int dev, int nsm, char *err, size_t errlen) {
+  static int graph_prepare(GraphSlot &G, int dev, int nsm, u32 kmax, char *err, size_t errlen) {
     if (G.exec && G.dev == dev) return 0;
     G.reset();
     SQ_CU(cudaMalloc((void **)&G.ctx, 2 * sizeof(Ctx) + sizeof(GraphStats)));
@@ -417,6 +421,7 @@ struct Engine {
     memset(&A, 0, sizeof(A));
     A.nsm = nsm;
     A.tags = 1;  // graph runs are sorts whose instances all carry tag scratch
+    A.kmax = kmax;
     // first round of the body, then the conditional second round
     SQ_CU(cudaStreamBeginCaptureToGraph(G.cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     cudaError_t ce = issue_round(L, G.ctx, nullptr, A);
@@ -806,8 +811,12 @@ struct Engine {
     if (graph) {
       // ---- every round on the device: one graph launch (relaunched only
       // after the host has grown the node pool)
-      GraphSlot &G = graph_slot();
-      rc = graph_prepare(G, dev, nsm, err, errlen);
+      // every node has k = ceil(sqrt n) <= ceil(sqrt(max_n)); round up to a power of two
+      int kb = 1;
+      while ((1u << kb) < std::min<u64>(isqrt_ceil(max_n), max_pivots() + 1)) ++kb;
+      const u32 kmax = std::min<u32>(1u << kb, max_pivots() + 1);
+      GraphSlot &G = graph_slot(kb);
+      rc = graph_prepare(G, dev, nsm, kmax, err, errlen);
       if (rc) return rc;
       struct Back {
         GraphStats gs;

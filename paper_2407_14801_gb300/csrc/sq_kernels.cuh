@@ -263,6 +263,12 @@ constexpr int kLeafMinBlocks() {
   return sizeof(typename KT<DT>::elem_t) != 8 ? 1 : WARP ? 3 : T <= 128 ? 6 : T >= 512 ? 2 : 1;
 }
 
+// Shared memory of a leaf CTA's sort (before its NaN lists).
+template <int DT, int T, int R, bool WARP>
+__host__ __device__ constexpr size_t leaf_sort_bytes() {
+  return (size_t)(WARP ? 8 : 1) * Sorter<KT<DT>, T, R, WARP>::SMEM * sizeof(typename KT<DT>::elem_t);
+}
+
 template <int DT, int T, int R, bool WARP>
 __global__ void __launch_bounds__(WARP ? 256 : T, kLeafMinBlocks<DT, T, WARP>()) k_leaf(const Ctx *__restrict__ cp, int cls, u32 count) {
   const Ctx &c = *cp;
@@ -275,7 +281,7 @@ __global__ void __launch_bounds__(WARP ? 256 : T, kLeafMinBlocks<DT, T, WARP>())
   constexpr int groups = WARP ? 8 : 1;
   const int g = WARP ? (threadIdx.x >> 5) : 0;
   const int tid = WARP ? (threadIdx.x & 31) : threadIdx.x;
-  u32 *nl = reinterpret_cast<u32 *>(smem + groups * S::SMEM) + g * kNanWords;  // K::lossy only
+  u32 *nl = reinterpret_cast<u32 *>(smem_raw + leaf_sort_bytes<DT, T, R, WARP>()) + g * kNanWords;  // K::lossy only
   const u32 cnt = count != kDev ? count : min(c.cnt_cur->leaves[cls], c.leaf_cap[cls]);
   // one leaf per warp (WARP) or per CTA; a fixed-size grid strides over the list
   for (u32 li = blockIdx.x * groups + g; li < cnt; li += gridDim.x * groups) {
@@ -297,7 +303,7 @@ __global__ void __launch_bounds__(WARP ? 256 : T, kLeafMinBlocks<DT, T, WARP>())
     if constexpr (K::lossy) {
       nn = nl[0];
       S::sync();  // read before the list is reset for the group's next leaf
-      if (nn > kNanCap) {
+      if (nn > kNanCap) {  // too many to restore: the fix list's exact (key, val) sort takes the leaf
         if (out)
           for (u32 p = tid; p < L.n; p += T) {
             ok[p] = ik[p];
@@ -343,7 +349,7 @@ __global__ void __launch_bounds__(T, (T <= 512 && sizeof(typename KT<DT>::elem_t
   const int rank = (int)cl.block_rank();
   const u32 cnt = count != kDev ? count : min(c.cnt_cur->leaves[cls], c.leaf_cap[cls]);
   const int tid = threadIdx.x;
-  u32 *nl = reinterpret_cast<u32 *>(s + S::SMEM);  // K::lossy only: this CTA's part's NaN list
+  u32 *nl = reinterpret_cast<u32 *>(smem_raw + leaf_sort_bytes<DT, T, R, false>());  // K::lossy only: this part's NaNs
   for (u32 li = blockIdx.x / G; li < cnt; li += gridDim.x / G) {  // the whole cluster
     const Leaf L = c.leaves_cur[cls][li];
     const Inst I = c.inst[L.inst];
@@ -372,7 +378,7 @@ __global__ void __launch_bounds__(T, (T <= 512 && sizeof(typename KT<DT>::elem_t
       }
       nn = nl[0];
       cl.sync();  // the counts are read before any list changes
-      if (most > kNanCap) {  // too many to restore: the fix list sorts the leaf
+      if (most > kNanCap) {  // too many to restore: the fix list's exact (key, val) sort takes the leaf
         if (out)
           for (u32 p = tid; p < nr; p += T) {
             ok[q0 + p] = ik[q0 + p];
@@ -1066,6 +1072,170 @@ __global__ void __launch_bounds__(256) k_skew(const Ctx *__restrict__ cp, u32 re
       }
       __syncthreads();
       if (tid < (int)kSkewBkts) sm.running[tid] += sm.tot[tid];
+      __syncthreads();
+    }
+  }
+}
+
+// SkewTranspose of a tile whose elements carry bucket tags (written by the
+// count): every chunk of the tile, taken in column-major order, is a stable
+// counting sort by tag -- which is exactly the order Algorithms 2 and 3
+// append in (bucket, then column, then position).  Warp w ranks a
+// contiguous part of the chunk (peers with the same tag from
+// __match_any_sync; a (tag, warp) counter kept by the group's lowest lane),
+// one scan over the (tag, warp) counters gives every element its slot in
+// shared memory, and the chunk leaves with one coalesced run per bucket.
+template <int DT, int CAP>
+struct SkewTagSmem {
+  typedef typename KT<DT>::elem_t E;
+  static constexpr int NW = 8;  // warps of a CTA
+  E out_e[CAP];
+  uint8_t out_j[CAP];
+  u32 cnt[kSkewBkts * (NW + 1)];  // (tag, warp), tag-major, padded rows
+  u32 base[kSkewBkts], running[kSkewBkts], ob[kSkewBkts + 1];
+  u32 seg_start[kSkewCols], seg_pre[kSkewCols + 1];
+  u32 wsc[33];
+  u32 s_u, s_ri, s_S;
+};
+
+template <int DT, int CAP>
+__global__ void __launch_bounds__(256, 4) k_skew_tags(const Ctx *__restrict__ cp, u32 ready_count) {
+  const Ctx &c = *cp;
+  if (ready_count == kDev) ready_count = min(c.cnt_cur->ready, c.ready_cap);
+  typedef KT<DT> K;
+  typedef typename K::elem_t E;
+  typedef typename K::key_t key_t;
+  typedef SkewTagSmem<DT, CAP> SM;
+  constexpr int NW = SM::NW, PW = CAP / NW, GR = PW / 32;  // per warp: PW elements in GR groups
+  static_assert(kSkewCols == 32 && kSkewBkts == 64 && PW % 32 == 0, "tile geometry");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SM &sm = *reinterpret_cast<SM *>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const u32 lt = (1u << lane) - 1u;
+  for (;;) {
+    grab_item(c, &c.status->cur_skew, c.status->tiles, 1, ready_count, &sm.s_u, &sm.s_ri);
+    __syncthreads();
+    const u32 u = sm.s_u;
+    if (u >= c.status->tiles) break;
+    const Node nd = c.nodes[c.ready_cur[sm.s_ri]];
+    const MetaLayout ML = meta_layout(nd.k, nd.cols, nd.ncb, nd.nkb, K::key_words);
+    const u32 *meta = c.meta + nd.meta;
+    const u32 tile = u - nd.tile_base;
+    const u32 Jb = tile / nd.ncs, Is = tile - Jb * nd.ncs;
+    const u32 j0 = Jb * kSkewBkts, nk = min((u32)kSkewBkts, nd.k - j0);
+    const u32 i0 = Is * kSkewCols, nc = min((u32)kSkewCols, nd.cols - i0);
+    const u32 *P = meta + ML.P;
+    if (warp == 0) {  // the tile's column segments and their prefix sums
+      u32 len_seg = 0, st = 0;
+      if ((u32)lane < nc) {
+        const u32 i = i0 + lane;
+        const u64 cs = (u64)i * nd.rows;
+        const u32 len = cs < nd.n ? (u32)min((u64)nd.rows, nd.n - cs) : 0;
+        u32 s0 = 0, s1 = 0;
+        if (len) {
+          s0 = P[(u64)Jb * nd.cols + i];
+          s1 = Jb + 1 < nd.nkb ? P[(u64)(Jb + 1) * nd.cols + i] : len;
+        }
+        st = (u32)cs + s0;
+        len_seg = s1 - s0;
+      }
+      u32 total;
+      const u32 ex = warp_excl_scan(len_seg, total);
+      sm.seg_start[lane] = st;
+      sm.seg_pre[lane] = ex;
+      if (lane == 0) {
+        sm.seg_pre[32] = total;
+        sm.s_S = total;
+      }
+    }
+    __syncthreads();
+    const u32 S = sm.s_S;
+    if (S == 0) continue;  // empty tile (common for sorted inputs)
+    const u32 *G = meta + ML.T;
+    const u32 *b = meta + ML.b;
+    if (tid < (int)nk) {
+      sm.base[tid] = b[j0 + tid] + G[(u64)(Is * (kSkewCols / kCountCols)) * nd.k + j0 + tid];
+      sm.running[tid] = 0;
+    }
+    const Inst I = c.inst[nd.inst];
+    const key_t *dk = (const key_t *)I.dkeys + nd.off;
+    const u32 *dv = I.dvals + nd.off;
+    const uint8_t *tg = I.tags + nd.off;
+    key_t *ak = (key_t *)I.keys + nd.off;
+    u32 *av = I.vals + nd.off;
+    for (u32 cs = 0; cs < S; cs += CAP) {
+      const u32 L = min((u32)CAP, S - cs);
+      for (int i = tid; i < kSkewBkts * (NW + 1); i += 256) sm.cnt[i] = 0;
+      __syncthreads();
+      // rank: warp `warp` takes chunk positions [warp*PW, warp*PW + PW)
+      E ev[GR];
+      u32 rt[GR];  // tag << 16 | rank within the warp's part
+#pragma unroll
+      for (int g = 0; g < GR; g++) {
+        const u32 ql = (u32)(warp * PW + g * 32 + lane);
+        const bool valid = ql < L;
+        u32 t = 0xffu;
+        ev[g] = K::top();
+        if (valid) {
+          const u32 q = cs + ql;
+          u32 ci = 0;  // column: the last with seg_pre <= q
+#pragma unroll
+          for (u32 st = 16; st > 0; st >>= 1)
+            if (ci + st < nc && sm.seg_pre[ci + st] <= q) ci += st;
+          const u32 p = sm.seg_start[ci] + (q - sm.seg_pre[ci]);
+          t = tg[p];
+          ev[g] = K::make(dk[p], dv[p]);
+        }
+        const u32 peers = __match_any_sync(0xffffffffu, t);
+        const u32 before = __popc(peers & lt);
+        u32 r0 = 0;
+        if (valid && before == 0) {  // the group's lowest lane reserves its slots
+          r0 = sm.cnt[t * (NW + 1) + warp];
+          sm.cnt[t * (NW + 1) + warp] = r0 + (u32)__popc(peers);
+        }
+        r0 = __shfl_sync(0xffffffffu, r0, __ffs(peers) - 1);
+        __syncwarp();
+        rt[g] = (t << 16) | (r0 + before);
+      }
+      __syncthreads();
+      // exclusive prefix over (tag, warp): thread tid holds 2 consecutive counters
+      u32 v0, v1;
+      {
+        const int L0 = 2 * tid, L1 = L0 + 1;
+        v0 = sm.cnt[(L0 / NW) * (NW + 1) + L0 % NW];
+        v1 = sm.cnt[(L1 / NW) * (NW + 1) + L1 % NW];
+        u32 total;
+        const u32 ex = block_excl_scan_u32(v0 + v1, sm.wsc, total);
+        sm.cnt[(L0 / NW) * (NW + 1) + L0 % NW] = ex;
+        sm.cnt[(L1 / NW) * (NW + 1) + L1 % NW] = ex + v0;
+        if ((L0 % NW) == 0) sm.ob[L0 / NW] = ex;  // first warp of a tag: the tag's start in the chunk
+        if (tid == 0) sm.ob[kSkewBkts] = total;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int g = 0; g < GR; g++) {
+        const u32 t = rt[g] >> 16;
+        if (t < (u32)kSkewBkts) {
+          const u32 slot = sm.cnt[t * (NW + 1) + warp] + (rt[g] & 0xffffu);
+          sm.out_e[slot] = ev[g];
+          sm.out_j[slot] = (uint8_t)t;
+        }
+      }
+      __syncthreads();
+      // one coalesced run per bucket
+      for (u32 s2 = tid; s2 < L; s2 += 256) {
+        const u32 jl = sm.out_j[s2];
+        const u32 dest = sm.base[jl] + sm.running[jl] + (s2 - sm.ob[jl]);
+        const E e = sm.out_e[s2];
+        if (dest < nd.n) {
+          ak[dest] = K::key(e);
+          av[dest] = K::val(e);
+        } else {
+          atomicOr(&c.status->error, ERRB_SIZES);
+        }
+      }
+      __syncthreads();
+      if (tid < (int)kSkewBkts) sm.running[tid] += sm.ob[tid + 1] - sm.ob[tid];
       __syncthreads();
     }
   }

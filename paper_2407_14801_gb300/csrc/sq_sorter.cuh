@@ -69,7 +69,10 @@ __device__ __forceinline__ void serial_merge(typename K::elem_t (&x)[R], int ai,
   }
 #pragma unroll
   for (int k = 0; k < R; k++) {
-    const bool tb = (bi < wb) && (ai >= wa || K::lt(b[0], a[0]));
+    // An exhausted run's head is top().  Where top() is bit-identical to any
+    // element equal to it, taking it in place of such an element outputs the
+    // same bits, and everything after it is top() as well: no bound checks.
+    const bool tb = K::top_is_value ? K::lt(b[0], a[0]) : (bi < wb) && (ai >= wa || K::lt(b[0], a[0]));
     x[k] = tb ? b[0] : a[0];
     if (k + 1 < R) {
       E nv = K::top();

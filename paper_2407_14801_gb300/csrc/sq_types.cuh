@@ -61,6 +61,7 @@ struct KT<DT_U32> {
   typedef u32 ord_t;
   static constexpr int key_words = 1;
   static constexpr bool lossy = false;
+  static constexpr bool top_is_value = true;  // top() is bit-identical to any element equal to it
   __device__ __forceinline__ static bool exact(key_t) { return true; }
   __device__ __forceinline__ static ord_t ord_key(key_t k) { return k; }
   __device__ __forceinline__ static key_t pad_key() { return 0xffffffffu; }
@@ -80,6 +81,7 @@ struct KT<DT_F32> {
   typedef u32 ord_t;
   static constexpr int key_words = 1;
   static constexpr bool lossy = false;
+  static constexpr bool top_is_value = false;  // an element may equal top() in order but carry other key bits
   __device__ __forceinline__ static bool exact(key_t) { return true; }
   __device__ __forceinline__ static ord_t ord_key(key_t k) { return f32_ordinal(k); }
   __device__ __forceinline__ static key_t pad_key() { return 0xffffffffu; }  // a NaN: ordinal max
@@ -113,6 +115,7 @@ struct KT<DT_F32W> {
   typedef u32 ord_t;
   static constexpr int key_words = 1;
   static constexpr bool lossy = true;
+  static constexpr bool top_is_value = true;  // top() is bit-identical to any element equal to it
   __device__ __forceinline__ static bool exact(key_t k) { return (k & 0x7fffffffu) <= 0x7f800000u; }
   __device__ __forceinline__ static ord_t ord_key(key_t k) { return f32_ordinal(k); }
   __device__ __forceinline__ static key_t pad_key() { return 0xffffffffu; }
@@ -132,6 +135,7 @@ struct KT<DT_U64> {
   typedef u64 ord_t;
   static constexpr int key_words = 2;
   static constexpr bool lossy = false;
+  static constexpr bool top_is_value = true;  // top() is bit-identical to any element equal to it
   __device__ __forceinline__ static bool exact(key_t) { return true; }
   __device__ __forceinline__ static ord_t ord_key(key_t k) { return k; }
   __device__ __forceinline__ static key_t pad_key() { return ~0ull; }
