@@ -1092,9 +1092,8 @@ struct SkewTagSmem {
   E out_e[CAP];
   uint8_t out_j[CAP];
   u32 cnt[kSkewBkts * (NW + 1)];  // (tag, warp), tag-major, padded rows
-  u32 base[kSkewBkts], running[kSkewBkts], ob[kSkewBkts + 1];
+  u32 base[kSkewBkts], running[kSkewBkts], ob[kSkewBkts + 1], adj[kSkewBkts];
   u32 seg_start[kSkewCols], seg_pre[kSkewCols + 1];
-  u32 wsc[33];
   u32 s_u, s_ri, s_S;
 };
 
@@ -1163,29 +1162,34 @@ __global__ void __launch_bounds__(256, 4) k_skew_tags(const Ctx *__restrict__ cp
     const uint8_t *tg = I.tags + nd.off;
     key_t *ak = (key_t *)I.keys + nd.off;
     u32 *av = I.vals + nd.off;
+    for (int i = tid; i < kSkewBkts * (NW + 1); i += 256) sm.cnt[i] = 0;
+    __syncthreads();
     for (u32 cs = 0; cs < S; cs += CAP) {
       const u32 L = min((u32)CAP, S - cs);
-      for (int i = tid; i < kSkewBkts * (NW + 1); i += 256) sm.cnt[i] = 0;
-      __syncthreads();
-      // rank: warp `warp` takes chunk positions [warp*PW, warp*PW + PW)
+      // warp `warp` takes chunk positions [warp*PW, warp*PW + PW): first every
+      // group's column, tag and element (independent loads), then the ranks
       E ev[GR];
-      u32 rt[GR];  // tag << 16 | rank within the warp's part
+      u32 rt[GR];  // tag, then tag << 16 | rank within the warp's part
 #pragma unroll
       for (int g = 0; g < GR; g++) {
         const u32 ql = (u32)(warp * PW + g * 32 + lane);
-        const bool valid = ql < L;
-        u32 t = 0xffu;
+        rt[g] = 0xffu;
         ev[g] = K::top();
-        if (valid) {
+        if (ql < L) {
           const u32 q = cs + ql;
           u32 ci = 0;  // column: the last with seg_pre <= q
 #pragma unroll
           for (u32 st = 16; st > 0; st >>= 1)
             if (ci + st < nc && sm.seg_pre[ci + st] <= q) ci += st;
           const u32 p = sm.seg_start[ci] + (q - sm.seg_pre[ci]);
-          t = tg[p];
+          rt[g] = tg[p];
           ev[g] = K::make(dk[p], dv[p]);
         }
+      }
+#pragma unroll
+      for (int g = 0; g < GR; g++) {
+        const u32 t = rt[g];
+        const bool valid = t < (u32)kSkewBkts;
         const u32 peers = __match_any_sync(0xffffffffu, t);
         const u32 before = __popc(peers & lt);
         u32 r0 = 0;
@@ -1198,18 +1202,37 @@ __global__ void __launch_bounds__(256, 4) k_skew_tags(const Ctx *__restrict__ cp
         rt[g] = (t << 16) | (r0 + before);
       }
       __syncthreads();
-      // exclusive prefix over (tag, warp): thread tid holds 2 consecutive counters
-      u32 v0, v1;
-      {
-        const int L0 = 2 * tid, L1 = L0 + 1;
-        v0 = sm.cnt[(L0 / NW) * (NW + 1) + L0 % NW];
-        v1 = sm.cnt[(L1 / NW) * (NW + 1) + L1 % NW];
+      // warp 0: per tag, the warps' exclusive offsets and the tag's start in
+      // the chunk; every counter becomes the slot of its warp's first element
+      if (warp == 0) {
+        u32 tot[2];
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+          const int t = 2 * lane + h;
+          u32 run = 0;
+#pragma unroll
+          for (int w2 = 0; w2 < NW; w2++) {
+            const u32 v = sm.cnt[t * (NW + 1) + w2];
+            sm.cnt[t * (NW + 1) + w2] = run;
+            run += v;
+          }
+          tot[h] = run;
+        }
         u32 total;
-        const u32 ex = block_excl_scan_u32(v0 + v1, sm.wsc, total);
-        sm.cnt[(L0 / NW) * (NW + 1) + L0 % NW] = ex;
-        sm.cnt[(L1 / NW) * (NW + 1) + L1 % NW] = ex + v0;
-        if ((L0 % NW) == 0) sm.ob[L0 / NW] = ex;  // first warp of a tag: the tag's start in the chunk
-        if (tid == 0) sm.ob[kSkewBkts] = total;
+        const u32 ex = warp_excl_scan(tot[0] + tot[1], total);
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+          const int t = 2 * lane + h;
+          const u32 o = ex + (h ? tot[0] : 0);
+          sm.ob[t] = o;
+#pragma unroll
+          for (int w2 = 0; w2 < NW; w2++) sm.cnt[t * (NW + 1) + w2] += o;
+          // output offset of the chunk's run of bucket t: dest = adj[t] + slot
+          if (t < (int)nk) {
+            sm.adj[t] = sm.base[t] + sm.running[t] - o;
+            sm.running[t] += tot[h];
+          }
+        }
       }
       __syncthreads();
 #pragma unroll
@@ -1222,10 +1245,9 @@ __global__ void __launch_bounds__(256, 4) k_skew_tags(const Ctx *__restrict__ cp
         }
       }
       __syncthreads();
-      // one coalesced run per bucket
+      // one coalesced run per bucket; the counters are free for the next chunk
       for (u32 s2 = tid; s2 < L; s2 += 256) {
-        const u32 jl = sm.out_j[s2];
-        const u32 dest = sm.base[jl] + sm.running[jl] + (s2 - sm.ob[jl]);
+        const u32 dest = sm.adj[sm.out_j[s2]] + s2;
         const E e = sm.out_e[s2];
         if (dest < nd.n) {
           ak[dest] = K::key(e);
@@ -1234,8 +1256,7 @@ __global__ void __launch_bounds__(256, 4) k_skew_tags(const Ctx *__restrict__ cp
           atomicOr(&c.status->error, ERRB_SIZES);
         }
       }
-      __syncthreads();
-      if (tid < (int)kSkewBkts) sm.running[tid] += sm.ob[tid + 1] - sm.ob[tid];
+      for (int i = tid; i < kSkewBkts * (NW + 1); i += 256) sm.cnt[i] = 0;
       __syncthreads();
     }
   }
