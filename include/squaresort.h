@@ -156,15 +156,20 @@ typedef struct {
 } sq_serve_opts;
 
 /* Create a server whose device memory pool holds at most hbm_budget_bytes
- * (requests' keys, vals and scratch).  A background thread admits queued
- * requests while the pool and the in-flight limit allow, and runs every
- * admitted request's recursion rounds together with the requests already
- * on the GPU (continuous batching).  opts may be NULL. */
+ * (requests' keys, vals and scratch, and the engines' work lists).  One
+ * persistent engine per key type runs the recursion rounds of every request
+ * of that type in flight, in the same launches; between two rounds it admits
+ * the queued requests that fit the pool and its in-flight limits (first
+ * come, first served within the key type), whose roots join the next
+ * round's work, and it hands back every request whose sort completed in
+ * the round just run (continuous batching).  max_inflight bounds the
+ * requests in flight per key type.  opts may be NULL. */
 sq_status sq_serve_create(sq_server **out, uint64_t hbm_budget_bytes, const sq_serve_opts *opts);
 
 /* Queue one sort.  desc->keys / desc->vals are HOST pointers that must stay
  * valid until sq_serve_poll reports completion; the result is written back
- * to them.  A request larger than the whole budget fails with
+ * to them.  A request whose data needs more than half the budget (or more
+ * elements than its key type's engine holds in flight) fails with
  * SQ_ERR_BUDGET.  *ticket identifies the request. */
 sq_status sq_serve_submit(sq_server *srv, const sq_sort_desc *desc, uint64_t *ticket);
 

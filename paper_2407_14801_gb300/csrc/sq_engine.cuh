@@ -923,6 +923,318 @@ struct Engine {
     }
     return rc;
   }
+
+  // ---- a persistent engine that instances join between rounds ------------
+  // (continuous batching).  Its lists, arena and instance slots are planned
+  // once for at most total_n_cap elements and ninst_cap instances in flight;
+  // admit() writes a new instance's root records into the lists of the next
+  // round, step() runs one round for everything in flight and reports the
+  // instances that completed in it.
+  struct Session {
+    SessionSpec sp;
+    cudaStream_t st = nullptr;
+    int nsm = 0;
+    Plan P;
+    char *slab = nullptr;
+    Node *nodes = nullptr;
+    u64 node_cap = 0;
+    Ctx hctx[2];
+    Ctx *cdev = nullptr;
+    Counters *cnt = nullptr;
+    Counters next;  // counts of the next round's lists (host copy)
+    u32 nodes_used = 0, done_seen = 0;
+    u64 round = 0;
+    void *pinned = nullptr;
+
+    cudaError_t dalloc(void **p, size_t bytes) {
+      if (sp.dev_alloc) {
+        *p = sp.dev_alloc(sp.alloc_ctx, bytes);
+        return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+      }
+      return cudaMallocAsync(p, bytes, st);
+    }
+    void dfree(void *p) {
+      if (!p) return;
+      if (sp.dev_free)
+        sp.dev_free(sp.alloc_ctx, p);
+      else
+        cudaFreeAsync(p, st);
+    }
+    ~Session() {
+      dfree(slab);
+      dfree(nodes);
+      if (pinned) cudaFreeHost(pinned);
+    }
+
+    bool has_work() const {
+      if (next.ready || next.fresh) return true;
+      for (int cl = 0; cl < kLeafClasses; cl++)
+        if (next.leaves[cl]) return true;
+      return false;
+    }
+
+    int open(const SessionSpec &spec, cudaStream_t stream, char *err, size_t errlen) {
+      sp = spec;
+      st = stream;
+      int dev = 0;
+      SQ_CU(cudaGetDevice(&dev));
+      SQ_CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+      if (sp.cutoff_min < 2 || sp.cutoff_max > max_leaf() || sp.cutoff_min > sp.cutoff_max) {
+        snprintf(err, errlen, "cutoffs [%u, %u] outside [2, %u]", sp.cutoff_min, sp.cutoff_max, max_leaf());
+        return 1;
+      }
+      P = make_plan(sp.total_n_cap, sp.ninst_cap, sp.cutoff_min, sp.cutoff_max, 0, 0, 0, 0);
+      node_cap = P.node_cap;
+      SQ_CU(dalloc((void **)&slab, P.slab_bytes));
+      SQ_CU(dalloc((void **)&nodes, sizeof(Node) * node_cap));
+      SQ_CU(cudaMallocHost(&pinned, 512));
+      Ctx c;
+      memset(&c, 0, sizeof(c));
+      c.inst = (Inst *)(slab + P.o_inst);
+      c.nodes = nodes;
+      c.node_cap = (u32)std::min<u64>(node_cap, 0xffffffffull);
+      for (int cl = 0; cl < kLeafClasses; cl++) c.leaf_cap[cl] = P.leaf_cap[cl];
+      c.ready_cap = (u32)P.ready_cap;
+      c.wbase = (u32 *)(slab + P.o_wbase);
+      c.fix = (Leaf *)(slab + P.o_fix);
+      c.fix_cap = (u32)std::min<u64>(P.fix_cap, 0xffffffffull);
+      c.fresh_cap = (u32)P.fresh_cap;
+      c.status = (Status *)(slab + P.o_status);
+      c.meta = (u32 *)(slab + P.o_meta);
+      c.meta_cap = P.meta_cap;
+      c.done_list = (u32 *)(slab + P.o_done);
+      c.cutoff = sp.cutoff_min;
+      for (int cl = 0; cl < kLeafClasses; cl++) c.class_cap[cl] = class_cap(cl);
+      c.recurse = 1;
+      c.ninst = sp.ninst_cap;  // also the length of the done_list ring
+      cnt = (Counters *)(slab + P.o_cnt);
+      for (int q = 0; q < 2; q++) {
+        hctx[q] = c;
+        for (int cl = 0; cl < kLeafClasses; cl++) {
+          hctx[q].leaves_cur[cl] = (Leaf *)(slab + P.o_leaves[q][cl]);
+          hctx[q].leaves_nxt[cl] = (Leaf *)(slab + P.o_leaves[q ^ 1][cl]);
+        }
+        hctx[q].ready_cur = (u32 *)(slab + P.o_ready[q]);
+        hctx[q].ready_nxt = (u32 *)(slab + P.o_ready[q ^ 1]);
+        hctx[q].fresh_cur = (u32 *)(slab + P.o_fresh[q]);
+        hctx[q].fresh_nxt = (u32 *)(slab + P.o_fresh[q ^ 1]);
+        hctx[q].cnt_cur = cnt + q;
+        hctx[q].cnt_nxt = cnt + (q ^ 1);
+      }
+      cdev = (Ctx *)(slab + P.o_ctx);
+      SQ_CU(cudaMemcpyAsync(cdev, hctx, sizeof(hctx), cudaMemcpyHostToDevice, st));
+      SQ_CU(cudaMemsetAsync(cnt, 0, 2 * sizeof(Counters), st));
+      SQ_CU(cudaMemsetAsync(slab + P.o_status, 0, sizeof(Status), st));
+      memset(&next, 0, sizeof(next));
+      SQ_CU(cudaStreamSynchronize(st));
+      return 0;
+    }
+
+    int grow_nodes(u64 need, char *err, size_t errlen) {
+      if (need <= node_cap) return 0;
+      const u64 ncap = std::max<u64>(2 * node_cap, need + P.fresh_cap);
+      Node *nn = nullptr;
+      SQ_CU(dalloc((void **)&nn, sizeof(Node) * ncap));
+      SQ_CU(cudaMemcpyAsync(nn, nodes, sizeof(Node) * nodes_used, cudaMemcpyDeviceToDevice, st));
+      SQ_CU(cudaStreamSynchronize(st));
+      dfree(nodes);
+      nodes = nn;
+      node_cap = ncap;
+      for (int q = 0; q < 2; q++) {
+        hctx[q].nodes = nodes;
+        hctx[q].node_cap = (u32)std::min<u64>(ncap, 0xffffffffull);
+      }
+      SQ_CU(cudaMemcpyAsync(cdev, hctx, sizeof(hctx), cudaMemcpyHostToDevice, st));
+      return 0;
+    }
+
+    // The instance in `slot` (free: its previous occupant completed) starts in
+    // the next round.  The caller keeps the elements in flight within the plan.
+    int admit(const InstSpec &is, u32 slot, char *err, size_t errlen) {
+      if (slot >= sp.ninst_cap || is.n == 0 || !is.tags) {
+        snprintf(err, errlen, "bad admission (slot %u, n %llu)", slot, (unsigned long long)is.n);
+        return 1;
+      }
+      const u64 lim = (u64)(max_pivots() + 1) * (max_pivots() + 1);
+      if (is.n > lim) {
+        snprintf(err, errlen, "n = %llu exceeds the largest supported size %llu", (unsigned long long)is.n,
+                 (unsigned long long)lim);
+        return 1;
+      }
+      const u32 cut = std::min(std::max(is.cutoff ? is.cutoff : sp.cutoff_max, sp.cutoff_min), sp.cutoff_max);
+      Inst hi;
+      memset(&hi, 0, sizeof(hi));
+      hi.keys = is.keys;
+      hi.vals = is.vals;
+      hi.dkeys = is.dkeys;
+      hi.dvals = is.dvals;
+      hi.tags = is.tags;
+      hi.n = is.n;
+      hi.cutoff = cut;
+      const int q = (int)(round & 1);  // the next round's lists
+      std::vector<Leaf> add[kLeafClasses];
+      auto put_leaf = [&](const Leaf &L) {
+        const int cl = class_of(L.n, NCLASS);
+        add[cl].push_back(L);
+        next.leaf_elems[cl] += L.n;
+      };
+      Node nd;
+      bool has_node = false, fresh = false;
+      if (is.n <= cut) {
+        Leaf L;
+        L.off = 0;
+        L.n = (u32)is.n;
+        L.inst = slot;
+        L.parent = kNone;
+        L.flags = KIND_ROOT;
+        put_leaf(L);
+      } else {
+        if (int rc = grow_nodes((u64)nodes_used + 1 + P.fresh_cap, err, errlen)) return rc;
+        memset(&nd, 0, sizeof(nd));
+        const u32 m = isqrt_ceil(is.n);
+        nd.off = 0;
+        nd.hash = root_hash(is.seed);
+        nd.n = (u32)is.n;
+        nd.rows = nd.cols = nd.k = m;
+        nd.inst = slot;
+        nd.parent = kNone;
+        nd.kind = KIND_ROOT;
+        nd.out = 0;
+        has_node = true;
+        const u32 id = nodes_used;
+        if (m <= cut && m >= kHostExpandCols) {  // its columns are leaves: spawn them here
+          const u32 ncol = (u32)((is.n + m - 1) / m);
+          nd.pending = (int)ncol;
+          for (u32 i = 0; i < ncol; i++) {
+            Leaf L;
+            L.off = (u64)i * m;
+            L.n = (u32)std::min<u64>(m, is.n - L.off);
+            L.inst = slot;
+            L.parent = id;
+            L.flags = KIND_COL | (1u << 8);
+            put_leaf(L);
+          }
+        } else {
+          fresh = true;
+        }
+      }
+      for (int cl = 0; cl < NCLASS; cl++)
+        if (next.leaves[cl] + add[cl].size() > P.leaf_cap[cl]) {
+          snprintf(err, errlen, "leaf list %d full", cl);
+          return 2;
+        }
+      if (fresh && next.fresh + 1 > P.fresh_cap) {
+        snprintf(err, errlen, "new-node list full");
+        return 2;
+      }
+      SQ_CU(cudaMemcpyAsync(hctx[0].inst + slot, &hi, sizeof(Inst), cudaMemcpyHostToDevice, st));
+      if (has_node) {
+        SQ_CU(cudaMemcpyAsync(nodes + nodes_used, &nd, sizeof(Node), cudaMemcpyHostToDevice, st));
+        if (fresh) {
+          const u32 id = nodes_used;
+          SQ_CU(cudaMemcpyAsync(hctx[q].fresh_cur + next.fresh, &id, 4, cudaMemcpyHostToDevice, st));
+          next.fresh++;
+        }
+        nodes_used++;
+        SQ_CU(cudaMemcpyAsync(&hctx[0].status->nodes_used, &nodes_used, 4, cudaMemcpyHostToDevice, st));
+      }
+      for (int cl = 0; cl < NCLASS; cl++)
+        if (!add[cl].empty()) {
+          SQ_CU(cudaMemcpyAsync(hctx[q].leaves_cur[cl] + next.leaves[cl], add[cl].data(),
+                                sizeof(Leaf) * add[cl].size(), cudaMemcpyHostToDevice, st));
+          next.leaves[cl] += (u32)add[cl].size();
+        }
+      SQ_CU(cudaMemcpyAsync(cnt + q, &next, sizeof(Counters), cudaMemcpyHostToDevice, st));
+      // pageable copies are staged before they return: the host records may go
+      return 0;
+    }
+
+    // One round for everything in flight; the slots of the instances that
+    // completed in it are appended to `completed`.
+    int step(std::vector<u32> &completed, char *err, size_t errlen) {
+      if (!has_work()) return 0;
+      Launcher L;
+      L.st = st;
+      L.prof = stats_box().profiling.load() != 0;
+      RoundArgs A;
+      memset(&A, 0, sizeof(A));
+      A.nsm = nsm;
+      A.tags = 1;
+      const int q = (int)(round & 1);
+      SQ_CU(issue_round(L, cdev + q, &next, A));
+      struct Readback {
+        Counters cnt;
+        Status status;
+      };
+      static_assert(sizeof(Readback) <= 512, "read-back buffer contract");
+      Readback *hrb = reinterpret_cast<Readback *>(pinned);
+      SQ_CU(cudaMemcpyAsync(&hrb->cnt, cnt + (q ^ 1), sizeof(Counters), cudaMemcpyDeviceToHost, st));
+      SQ_CU(cudaMemcpyAsync(&hrb->status, hctx[0].status, sizeof(Status), cudaMemcpyDeviceToHost, st));
+      SQ_CU(cudaStreamSynchronize(st));
+      L.collect();
+      const Status S = hrb->status;
+      next = hrb->cnt;
+      nodes_used = S.nodes_used;
+      round++;
+      {
+        std::lock_guard<std::mutex> g(stats_box().mu);
+        EngineStats &G = stats_box().s;
+        for (int f = 0; f < KF_COUNT_FAMILIES; f++) {
+          G.launches[f] += L.local.launches[f];
+          G.ms[f] += L.local.ms[f];
+          G.bytes[f] += L.local.bytes[f];
+        }
+        G.rounds += 1;
+        G.nodes += L.local.nodes;
+        G.sorts += S.done - done_seen;
+      }
+      if (S.error & ~ERRB_TRACE) {
+        snprintf(err, errlen, "engine error bits 0x%x (1 pivot attempts, 2 nodes, 4 list, 8 arena, 16 sizes)",
+                 S.error);
+        return (S.error & ERRB_ATTEMPTS) ? 7 : ((S.error & ERRB_SIZES) ? 8 : 2);
+      }
+      if (S.done != done_seen) {  // the ring of completed slots
+        const u32 nd = S.done - done_seen, cap = sp.ninst_cap;
+        std::vector<u32> got(nd);
+        const u32 a = done_seen % cap, first = std::min(nd, cap - a);
+        SQ_CU(cudaMemcpyAsync(got.data(), hctx[0].done_list + a, 4 * first, cudaMemcpyDeviceToHost, st));
+        if (first < nd)
+          SQ_CU(cudaMemcpyAsync(got.data() + first, hctx[0].done_list, 4 * (nd - first), cudaMemcpyDeviceToHost, st));
+        SQ_CU(cudaStreamSynchronize(st));
+        completed.insert(completed.end(), got.begin(), got.end());
+        done_seen = S.done;
+      }
+      return grow_nodes((u64)nodes_used + P.fresh_cap, err, errlen);
+    }
+  };
+
+  static u64 session_scratch_bytes(const SessionSpec &sp) {
+    const Plan P = make_plan(sp.total_n_cap, sp.ninst_cap, sp.cutoff_min, sp.cutoff_max, 0, 0, 0, 0);
+    return ((P.slab_bytes + 255) & ~(u64)255) + sizeof(Node) * P.node_cap + 4096;
+  }
 };
+
+
+// Session entry points of one key type (expanded once per engine unit).
+#define SQ_SESSION_FUNCS(SUFFIX, DTV)                                                                      \
+  int session_open_##SUFFIX(const SessionSpec &sp, cudaStream_t st, void **out, char *err, size_t errlen) { \
+    auto *s = new Engine<DTV>::Session();                                                                   \
+    const int rc = s->open(sp, st, err, errlen);                                                            \
+    if (rc) {                                                                                               \
+      delete s;                                                                                             \
+      return rc;                                                                                            \
+    }                                                                                                       \
+    *out = s;                                                                                               \
+    return 0;                                                                                               \
+  }                                                                                                         \
+  int session_admit_##SUFFIX(void *s, const InstSpec &is, uint32_t slot, char *err, size_t errlen) {        \
+    return static_cast<Engine<DTV>::Session *>(s)->admit(is, slot, err, errlen);                            \
+  }                                                                                                         \
+  int session_step_##SUFFIX(void *s, std::vector<uint32_t> &done, char *err, size_t errlen) {               \
+    return static_cast<Engine<DTV>::Session *>(s)->step(done, err, errlen);                                 \
+  }                                                                                                         \
+  bool session_busy_##SUFFIX(void *s) { return static_cast<Engine<DTV>::Session *>(s)->has_work(); }       \
+  void session_close_##SUFFIX(void *s) { delete static_cast<Engine<DTV>::Session *>(s); }                  \
+  uint64_t session_scratch_bytes_##SUFFIX(const SessionSpec &sp) { return Engine<DTV>::session_scratch_bytes(sp); }
 
 }  // namespace sq

@@ -2,6 +2,7 @@
 // type).  Plain C++: no CUDA device code here.
 #pragma once
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 namespace sq {
@@ -78,6 +79,27 @@ uint64_t engine_skew_scratch_bytes(int dtype, uint64_t n, uint64_t cols, uint64_
 
 // Upper bound of the engine's own scratch bytes for a run (admission control).
 uint64_t engine_scratch_bytes(int dtype, uint64_t total_n, uint32_t ninst, uint32_t cutoff, uint32_t cutoff_max);
+
+// A persistent engine that instances join between rounds (continuous
+// batching): planned once for total_n_cap elements and ninst_cap instances
+// in flight.  Scratch from dev_alloc (NULL: cudaMallocAsync on the stream).
+struct SessionSpec {
+  uint64_t total_n_cap;
+  uint32_t ninst_cap;
+  uint32_t cutoff_min, cutoff_max;  // the instances' cutoffs lie in this range
+  void *(*dev_alloc)(void *ctx, size_t bytes);
+  void (*dev_free)(void *ctx, void *p);
+  void *alloc_ctx;
+};
+// Returns 0 or a status code; *out is an opaque session of key type dtype.
+int session_open(int dtype, const SessionSpec &sp, cudaStream_t st, void **out, char *err, size_t errlen);
+// Starts instance `is` (tags required; n > 0) in slot `slot` at the next round.
+int session_admit(int dtype, void *s, const InstSpec &is, uint32_t slot, char *err, size_t errlen);
+// Runs one round if anything is in flight; appends the completed slots.
+int session_step(int dtype, void *s, std::vector<uint32_t> &completed, char *err, size_t errlen);
+bool session_busy(int dtype, void *s);
+void session_close(int dtype, void *s);
+uint64_t session_scratch_bytes(int dtype, const SessionSpec &sp);
 
 // Returns 0 or a status code (sq_status values); writes a message on error.
 int engine_run_u32(const RunSpec &spec, cudaStream_t st, char *err, size_t errlen);

@@ -11,4 +11,6 @@ int engine_run_f32(const RunSpec &spec, cudaStream_t st, char *err, size_t errle
   return Engine<DT_F32>::run(spec, st, err, errlen);
 }
 
+SQ_SESSION_FUNCS(f32, DT_F32)
+
 }  // namespace sq

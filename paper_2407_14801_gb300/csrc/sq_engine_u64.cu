@@ -11,4 +11,6 @@ int engine_run_u64(const RunSpec &spec, cudaStream_t st, char *err, size_t errle
   return Engine<DT_U64>::run(spec, st, err, errlen);
 }
 
+SQ_SESSION_FUNCS(u64, DT_U64)
+
 }  // namespace sq

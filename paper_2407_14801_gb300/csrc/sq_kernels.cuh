@@ -199,7 +199,7 @@ static __device__ void child_done(const Ctx &c, u32 parent, u32 kind, u32 inst) 
   for (;;) {
     if (parent == kNone) {
       const u32 d = atomicAdd(&c.status->done, 1u);
-      c.done_list[d] = inst;
+      c.done_list[d % c.ninst] = inst;  // a ring in a persistent session
       return;
     }
     Node *p = &c.nodes[parent];

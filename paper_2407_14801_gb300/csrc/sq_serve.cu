@@ -1,16 +1,19 @@
 // Serving loop: a FIFO of sort requests, a device memory pool bounded by an
-// HBM budget, and several sessions (host thread + CUDA stream each).  A free
-// session admits every queued request that fits the pool (first come, first
-// served) and runs them as one batch through the engine; the other sessions
-// keep running theirs, so requests that arrive while others are on the GPU
-// start as soon as a session and memory free up, and their kernels overlap
-// on the device with the batches already running.
+// HBM budget, and one persistent engine session per key type, each with a
+// copy-in and a copy-out stage (host thread + CUDA stream each).  Between any two recursion rounds a session admits the
+// queued requests of its key type that fit (first come, first served within
+// the type): their roots join the next round's work lists, so a request
+// that arrives while others are on the GPU starts at the next round
+// boundary and its kernels are the same launches as theirs (continuous
+// batching).  A request leaves the session, and its result is copied back,
+// as soon as the round in which its last leaf finished ends.
 #include <chrono>
 #include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <deque>
+#include <string>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -67,170 +70,267 @@ struct sq_server {
   std::deque<Req *> queue;
   std::unordered_map<uint64_t, Req *> reqs;
   uint64_t next_ticket = 1;
-  uint32_t inflight = 0;
   bool stopping = false;
   std::vector<std::thread> workers;
+  // one engine session per key type (a request joins its type's session)
+  uint64_t total_n_cap[3] = {0, 0, 0};
+  uint64_t inflight_n[3] = {0, 0, 0};
+  uint32_t reserved[3] = {0, 0, 0};  // requests copied in or in flight
+  std::deque<Req *> joinq[3];        // copied in, waiting for the next round boundary
+  std::deque<Req *> outq[3];         // sorted, waiting to be copied out
+  std::string open_error[3];
+  bool open_failed[3] = {false, false, false};
+  bool session_gone[3] = {false, false, false};
 };
 
 namespace {
 
-uint64_t scratch_need(sq_server *s, const std::vector<Req *> &b, int dtype) {
-  uint64_t tot = 0;
-  uint32_t cnt = 0, c = s->cutoff ? s->cutoff : sq_get_cutoff((sq_dtype)dtype), cmax = c;
-  for (Req *r : b)
-    if (r->d.dtype == dtype) {
-      tot += r->d.n;
-      cnt++;
-      // work lists are sized for the smallest cutoff, leaf classes for the largest
-      if (!s->cutoff) {
-        const uint32_t ci = sq_cutoff_for((sq_dtype)dtype, r->d.n);
-        c = std::min(c, ci);
-        cmax = std::max(cmax, ci);
-      }
-    }
-  if (!cnt) return 0;
-  return sq::engine_scratch_bytes(dtype, tot, cnt, c, cmax) + 4096;
-}
-
-uint64_t batch_scratch(sq_server *s, const std::vector<Req *> &b) {
-  uint64_t m = 0;  // dtype groups run one after another: the largest need
-  for (int d = 0; d < 3; d++) m = std::max(m, scratch_need(s, b, d));
-  return m;
-}
-
-struct Bump {
-  char *base;
-  uint64_t size, used;
-};
-void *bump_alloc(void *ctx, size_t bytes) {
-  Bump *b = (Bump *)ctx;
-  const uint64_t need = al(bytes);
-  if (b->used + need > b->size) return nullptr;
-  void *p = b->base + b->used;
-  b->used += need;
-  return p;
-}
-void bump_free(void *, void *) {}
-
-void run_batch(sq_server *s, cudaStream_t st, std::vector<Req *> &batch, uint64_t soff, uint64_t ssize) {
-  cudaError_t e = cudaSuccess;
-  for (Req *r : batch) {  // copy in
-    const uint64_t n = r->d.n, w = kbytes(r->d.dtype);
-    char *base = s->slab + r->off;
-    if (n && e == cudaSuccess) e = cudaMemcpyAsync(base, r->d.keys, n * w, cudaMemcpyHostToDevice, st);
-    if (n && e == cudaSuccess && r->d.vals)
-      e = cudaMemcpyAsync(base + al(n * w), r->d.vals, n * 4, cudaMemcpyHostToDevice, st);
-  }
-  std::vector<sq_status> st_of(batch.size(), e == cudaSuccess ? SQ_OK : SQ_ERR_CUDA);
-  for (int d = 0; d < 3 && e == cudaSuccess; d++) {
-    std::vector<sq::InstSpec> is;
-    std::vector<size_t> who;
-    for (size_t q = 0; q < batch.size(); q++) {
-      Req *r = batch[q];
-      if (r->d.dtype != d || r->d.n == 0) continue;
-      const uint64_t n = r->d.n, w = kbytes(r->d.dtype);
-      char *base = s->slab + r->off;
-      sq::InstSpec x{};
-      x.keys = base;
-      x.vals = (uint32_t *)(base + al(n * w));
-      x.dkeys = base + al(n * w) + al(n * 4);
-      x.dvals = (uint32_t *)(base + al(n * w) + al(n * 4) + al(n * w));
-      x.tags = (uint8_t *)(base + al(n * w) + al(n * 4) + al(n * w) + al(n * 4));
-      x.n = n;
-      x.seed = r->d.seed;
-      x.cutoff = s->cutoff ? s->cutoff : sq_cutoff_for((sq_dtype)d, n);
-      is.push_back(x);
-      who.push_back(q);
-    }
-    if (is.empty()) continue;
-    // payloads for requests without vals: the original index
-    for (size_t q = 0; q < who.size(); q++)
-      if (!batch[who[q]]->d.vals) {
-        std::vector<uint32_t> iota(is[q].n);
-        for (uint64_t i = 0; i < is[q].n; i++) iota[i] = (uint32_t)i;
-        cudaMemcpyAsync(is[q].vals, iota.data(), 4 * is[q].n, cudaMemcpyHostToDevice, st);
-        cudaStreamSynchronize(st);
-      }
-    Bump bump{s->slab + soff, ssize, 0};
-    sq::RunSpec spec;
-    memset(&spec, 0, sizeof(spec));
-    spec.inst = is.data();
-    spec.ninst = (uint32_t)is.size();
-    spec.cutoff = s->cutoff ? s->cutoff : sq_get_cutoff((sq_dtype)d);
-    spec.graph = sq_get_launch_mode() == SQ_LAUNCH_GRAPH;
-    spec.dev_alloc = bump_alloc;
-    spec.dev_free = bump_free;
-    spec.alloc_ctx = &bump;
-    char err[256] = {0};
-    int rc = 0;
-    switch (d) {
-      case SQ_U32: rc = sq::engine_run_u32(spec, st, err, sizeof(err)); break;
-      case SQ_U64: rc = sq::engine_run_u64(spec, st, err, sizeof(err)); break;
-      default: rc = sq::engine_run_f32(spec, st, err, sizeof(err)); break;
-    }
-    if (rc)
-      for (size_t q : who) st_of[q] = (sq_status)rc;
-  }
-  for (size_t q = 0; q < batch.size(); q++) {  // copy out
-    Req *r = batch[q];
-    const uint64_t n = r->d.n, w = kbytes(r->d.dtype);
-    if (!n || st_of[q] != SQ_OK) continue;
-    char *base = s->slab + r->off;
-    if (cudaMemcpyAsync(r->d.keys, base, n * w, cudaMemcpyDeviceToHost, st) != cudaSuccess) st_of[q] = SQ_ERR_CUDA;
-    if (r->d.vals && cudaMemcpyAsync(r->d.vals, base + al(n * w), n * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
-      st_of[q] = SQ_ERR_CUDA;
-  }
-  if (cudaStreamSynchronize(st) != cudaSuccess)
-    for (auto &x : st_of) x = SQ_ERR_CUDA;
-  const double t1 = now_s();
+// Engine scratch (node pool growth included) comes from the same pool as
+// the requests' data.
+void *pool_alloc(void *ctx, size_t bytes) {
+  sq_server *s = (sq_server *)ctx;
   std::lock_guard<std::mutex> lk(s->mu);
-  s->pool.release(soff);
-  for (size_t q = 0; q < batch.size(); q++) {
-    Req *r = batch[q];
-    s->pool.release(r->off);
-    r->result = st_of[q];
-    r->latency = t1 - r->t0;
-    r->done = true;
-  }
-  s->inflight -= (uint32_t)batch.size();
-  s->cv.notify_all();
+  uint64_t off = 0;
+  if (!s->pool.alloc(al(bytes), &off)) return nullptr;
+  return s->slab + off;
+}
+void pool_free(void *ctx, void *p) {
+  sq_server *s = (sq_server *)ctx;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->pool.release((uint64_t)((char *)p - s->slab));
 }
 
-void worker(sq_server *s) {
+__global__ void k_serve_iota(uint32_t *v, uint64_t n) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    v[i] = (uint32_t)i;
+}
+
+// The key type's cutoffs: the server's, or the range of the tuned table.
+void cutoff_range(sq_server *s, int d, uint32_t &lo, uint32_t &hi) {
+  if (s->cutoff) {
+    lo = hi = s->cutoff;
+    return;
+  }
+  lo = hi = sq_get_cutoff((sq_dtype)d);
+  for (int lg = 0; lg < 63; lg++) {
+    const uint32_t c = sq_cutoff_for((sq_dtype)d, 1ull << lg);
+    lo = std::min(lo, c);
+    hi = std::max(hi, c);
+  }
+}
+
+void finish(sq_server *s, Req *r, sq_status st) {
+  // caller holds s->mu
+  r->result = st;
+  r->latency = now_s() - r->t0;
+  r->done = true;
+  s->pool.release(r->off);
+  s->inflight_n[r->d.dtype] -= r->d.n;
+  s->reserved[r->d.dtype]--;
+}
+
+// The InstSpec of a request's pool range: keys | vals | D keys | D vals | tags.
+sq::InstSpec layout(sq_server *s, Req *r) {
+  const uint64_t n = r->d.n, w = kbytes(r->d.dtype);
+  char *base = s->slab + r->off;
+  sq::InstSpec x{};
+  x.keys = base;
+  x.vals = (uint32_t *)(base + al(n * w));
+  x.dkeys = base + al(n * w) + al(n * 4);
+  x.dvals = (uint32_t *)(base + al(n * w) + al(n * 4) + al(n * w));
+  x.tags = (uint8_t *)(base + al(n * w) + al(n * 4) + al(n * w) + al(n * 4));
+  x.n = n;
+  x.seed = r->d.seed;
+  x.cutoff = s->cutoff ? s->cutoff : sq_cutoff_for(r->d.dtype, n);
+  return x;
+}
+
+// Copy-in stage of one key type: takes queued requests of the type in order
+// while a pool range, an engine slot and room under the type's in-flight
+// limit are free, copies them in on its own stream and hands them to the
+// session thread, which admits them at its next round boundary.
+void copier_in(sq_server *s, int d) {
   cudaSetDevice(s->device);
   cudaStream_t st;
   cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  const uint64_t w = kbytes((sq_dtype)d);
   for (;;) {
-    std::vector<Req *> batch;
-    uint64_t soff = 0, ssize = 0;
+    Req *r = nullptr;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      s->cv.wait(lk, [&] {
-        if (s->stopping) return true;
-        if (s->queue.empty() || s->inflight >= s->max_inflight) return false;
-        Req *f = s->queue.front();
-        return s->pool.fits(f->data) && s->pool.largest_free() >= f->data + scratch_need(s, {f}, f->d.dtype);
-      });
-      if (s->stopping && s->queue.empty()) break;
-      while (!s->queue.empty() && s->inflight + batch.size() < s->max_inflight) {
-        Req *r = s->queue.front();
-        if (!s->pool.alloc(r->data, &r->off)) break;
-        batch.push_back(r);
-        s->queue.pop_front();
+      auto head = [&]() -> Req * {
+        for (Req *q : s->queue)
+          if (q->d.dtype == d) return q;
+        return nullptr;
+      };
+      auto can_take = [&](Req *q) {
+        return q && (s->session_gone[d] ||
+                     (s->reserved[d] < s->max_inflight && s->inflight_n[d] + q->d.n <= s->total_n_cap[d] &&
+                      s->pool.fits(q->data)));
+      };
+      s->cv.wait(lk, [&] { return (s->stopping && !head()) || can_take(head()); });
+      r = head();
+      if (!r) break;  // stopping, nothing of this type queued
+      for (auto it = s->queue.begin(); it != s->queue.end(); ++it)
+        if (*it == r) {
+          s->queue.erase(it);
+          break;
+        }
+      if (s->session_gone[d]) {
+        r->result = SQ_ERR_NOMEM;
+        r->latency = now_s() - r->t0;
+        r->done = true;
+        continue;
       }
-      // scratch for the batch; give back the newest requests until it fits
-      while (!batch.empty()) {
-        ssize = batch_scratch(s, batch);
-        if (s->pool.alloc(ssize, &soff)) break;
-        Req *r = batch.back();
-        batch.pop_back();
-        s->pool.release(r->off);
+      if (!s->pool.alloc(r->data, &r->off)) {  // raced with another allocation: queue head again
         s->queue.push_front(r);
+        continue;
       }
-      s->inflight += (uint32_t)batch.size();
+      s->inflight_n[d] += r->d.n;
+      s->reserved[d]++;
     }
-    if (!batch.empty()) run_batch(s, st, batch, soff, ssize);
+    const sq::InstSpec x = layout(s, r);
+    const uint64_t n = r->d.n;
+    cudaError_t e = cudaMemcpyAsync(x.keys, r->d.keys, n * w, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+      if (r->d.vals)
+        e = cudaMemcpyAsync(x.vals, r->d.vals, n * 4, cudaMemcpyHostToDevice, st);
+      else
+        k_serve_iota<<<(unsigned)std::min<uint64_t>((n + 255) / 256, 4096), 256, 0, st>>>(x.vals, n);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (e != cudaSuccess)
+      finish(s, r, SQ_ERR_CUDA);
+    else
+      s->joinq[d].push_back(r);
+    s->cv.notify_all();
   }
+  cudaStreamDestroy(st);
+}
+
+// Copy-out stage: results of the requests the session finished.
+void copier_out(sq_server *s, int d) {
+  cudaSetDevice(s->device);
+  cudaStream_t st;
+  cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  const uint64_t w = kbytes((sq_dtype)d);
+  for (;;) {
+    std::vector<Req *> batch;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv.wait(lk, [&] { return !s->outq[d].empty() || (s->stopping && s->reserved[d] == 0); });
+      if (s->outq[d].empty()) break;
+      batch.assign(s->outq[d].begin(), s->outq[d].end());
+      s->outq[d].clear();
+    }
+    std::vector<sq_status> res(batch.size(), SQ_OK);
+    for (size_t i = 0; i < batch.size(); i++) {
+      Req *r = batch[i];
+      const uint64_t n = r->d.n;
+      char *base = s->slab + r->off;
+      if (cudaMemcpyAsync(r->d.keys, base, n * w, cudaMemcpyDeviceToHost, st) != cudaSuccess) res[i] = SQ_ERR_CUDA;
+      if (r->d.vals && cudaMemcpyAsync(r->d.vals, base + al(n * w), n * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        res[i] = SQ_ERR_CUDA;
+    }
+    const bool ok = cudaStreamSynchronize(st) == cudaSuccess;
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (size_t i = 0; i < batch.size(); i++) finish(s, batch[i], ok ? res[i] : SQ_ERR_CUDA);
+    s->cv.notify_all();
+  }
+  cudaStreamDestroy(st);
+}
+
+// Session stage of one key type: between rounds, admit what the copy-in
+// stage finished (each takes a free slot); run one round; pass the requests
+// that completed in it to the copy-out stage.
+void worker(sq_server *s, int d) {
+  cudaSetDevice(s->device);
+  cudaStream_t st;
+  cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  sq::SessionSpec sp;
+  memset(&sp, 0, sizeof(sp));
+  sp.total_n_cap = s->total_n_cap[d];
+  sp.ninst_cap = s->max_inflight;
+  cutoff_range(s, d, sp.cutoff_min, sp.cutoff_max);
+  sp.dev_alloc = pool_alloc;
+  sp.dev_free = pool_free;
+  sp.alloc_ctx = s;
+  void *sess = nullptr;
+  char err[256] = {0};
+  if (sq::session_open(d, sp, st, &sess, err, sizeof(err)) != 0) sess = nullptr;
+  if (!sess) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->open_failed[d] = true;
+    s->session_gone[d] = true;
+    s->open_error[d] = err;
+    for (Req *r : s->joinq[d]) finish(s, r, SQ_ERR_NOMEM);
+    s->joinq[d].clear();
+    s->cv.notify_all();
+  }
+  std::vector<Req *> slot_req(s->max_inflight, nullptr);
+  std::vector<uint32_t> free_slots;
+  for (uint32_t i = s->max_inflight; i-- > 0;) free_slots.push_back(i);
+  while (sess) {
+    std::vector<Req *> join;
+    const bool busy = sq::session_busy(d, sess);
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      if (!busy)
+        s->cv.wait(lk, [&] { return !s->joinq[d].empty() || (s->stopping && s->reserved[d] == 0); });
+      if (!busy && s->joinq[d].empty()) break;  // stopping and drained
+      while (!s->joinq[d].empty() && !free_slots.empty()) {
+        join.push_back(s->joinq[d].front());
+        s->joinq[d].pop_front();
+      }
+    }
+    for (Req *r : join) {
+      const uint32_t slot = free_slots.back();
+      free_slots.pop_back();
+      const int rc = sq::session_admit(d, sess, layout(s, r), slot, err, sizeof(err));
+      if (rc) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        finish(s, r, (sq_status)rc);
+        free_slots.push_back(slot);
+        s->cv.notify_all();
+      } else {
+        slot_req[slot] = r;
+      }
+    }
+    if (!sq::session_busy(d, sess)) continue;
+    std::vector<uint32_t> done;
+    const int rc = sq::session_step(d, sess, done, err, sizeof(err));
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (rc) {  // the session's state is lost: fail what it holds and start afresh
+      for (uint32_t i = 0; i < s->max_inflight; i++)
+        if (slot_req[i]) {
+          finish(s, slot_req[i], (sq_status)rc);
+          slot_req[i] = nullptr;
+        }
+      free_slots.clear();
+      for (uint32_t i = s->max_inflight; i-- > 0;) free_slots.push_back(i);
+      sq::session_close(d, sess);
+      sess = nullptr;
+      if (sq::session_open(d, sp, st, &sess, err, sizeof(err)) != 0) {
+        sess = nullptr;
+        s->session_gone[d] = true;
+        for (Req *r : s->joinq[d]) finish(s, r, SQ_ERR_NOMEM);
+        s->joinq[d].clear();
+      }
+      s->cv.notify_all();
+      continue;
+    }
+    for (uint32_t slot : done) {
+      Req *r = slot < slot_req.size() ? slot_req[slot] : nullptr;
+      if (!r) continue;
+      slot_req[slot] = nullptr;
+      free_slots.push_back(slot);
+      s->outq[d].push_back(r);
+    }
+    if (!done.empty()) s->cv.notify_all();
+  }
+  if (sess) sq::session_close(d, sess);
+  cudaStreamSynchronize(st);
   cudaStreamDestroy(st);
 }
 
@@ -256,8 +356,25 @@ sq_status sq_serve_create(sq_server **out, uint64_t hbm_budget_bytes, const sq_s
                  cudaGetErrorString(e));
   }
   s->pool.reset(hbm_budget_bytes);
-  const int sessions = 4;
-  for (int i = 0; i < sessions; i++) s->workers.emplace_back(worker, s);
+  // every key type may hold up to half the budget's worth of elements in
+  // flight (data of 2(w+4)+1 bytes an element), as long as its session's
+  // work lists -- planned for that many -- take at most a tenth of the budget
+  for (int d = 0; d < 3; d++) {
+    sq::SessionSpec sp;
+    memset(&sp, 0, sizeof(sp));
+    sp.ninst_cap = s->max_inflight;
+    cutoff_range(s, d, sp.cutoff_min, sp.cutoff_max);
+    sp.total_n_cap = hbm_budget_bytes / 2 / (2 * (kbytes((sq_dtype)d) + 4) + 3);
+    while (sp.total_n_cap > 4096 && sq::session_scratch_bytes(d, sp) > hbm_budget_bytes / 10) sp.total_n_cap /= 2;
+    s->total_n_cap[d] = sp.total_n_cap;
+  }
+  for (int d = 0; d < 3; d++) {  // copies from and to pageable host memory: two threads a direction
+    s->workers.emplace_back(worker, s, d);
+    for (int c = 0; c < 2; c++) {
+      s->workers.emplace_back(copier_in, s, d);
+      s->workers.emplace_back(copier_out, s, d);
+    }
+  }
   *out = s;
   return SQ_OK;
 }
@@ -272,11 +389,14 @@ sq_status sq_serve_submit(sq_server *s, const sq_sort_desc *desc, uint64_t *tick
   r->data = data_bytes(*desc);
   r->t0 = now_s();
   std::lock_guard<std::mutex> lk(s->mu);
-  const uint64_t need = r->data + scratch_need(s, {r}, desc->dtype) + 256;
-  if (need > s->pool.capacity()) {
+  if (r->data > s->pool.capacity() / 2 || desc->n > s->total_n_cap[desc->dtype]) {
     delete r;
-    return sfail(SQ_ERR_BUDGET, "request needs %llu bytes, budget is %llu", (unsigned long long)need,
-                 (unsigned long long)s->pool.capacity());
+    return sfail(SQ_ERR_BUDGET, "request needs %llu bytes, at most half the budget (%llu) is available to one request",
+                 (unsigned long long)al(data_bytes(*desc)), (unsigned long long)s->pool.capacity());
+  }
+  if (s->open_failed[desc->dtype]) {
+    delete r;
+    return sfail(SQ_ERR_NOMEM, "no engine for this key type: %s", s->open_error[desc->dtype].c_str());
   }
   if (s->stopping) {
     delete r;
@@ -284,8 +404,12 @@ sq_status sq_serve_submit(sq_server *s, const sq_sort_desc *desc, uint64_t *tick
   }
   r->ticket = s->next_ticket++;
   s->reqs[r->ticket] = r;
-  s->queue.push_back(r);
   *ticket = r->ticket;
+  if (desc->n == 0) {  // nothing to sort
+    r->done = true;
+    return SQ_OK;
+  }
+  s->queue.push_back(r);
   s->cv.notify_all();
   return SQ_OK;
 }
