@@ -282,9 +282,19 @@ __global__ void __launch_bounds__(WARP ? 256 : T, kLeafMinBlocks<DT, T, WARP>())
   const int g = WARP ? (threadIdx.x >> 5) : 0;
   const int tid = WARP ? (threadIdx.x & 31) : threadIdx.x;
   u32 *nl = reinterpret_cast<u32 *>(smem_raw + leaf_sort_bytes<DT, T, R, WARP>()) + g * kNanWords;  // K::lossy only
-  const u32 cnt = count != kDev ? count : min(c.cnt_cur->leaves[cls], c.leaf_cap[cls]);
-  // one leaf per warp (WARP) or per CTA; a fixed-size grid strides over the list
-  for (u32 li = blockIdx.x * groups + g; li < cnt; li += gridDim.x * groups) {
+  const bool dyn = count == kDev;  // a fixed-size grid: every group takes the next leaf
+  const u32 cnt = dyn ? min(c.cnt_cur->leaves[cls], c.leaf_cap[cls]) : count;
+  __shared__ u32 s_li[groups];
+  auto next_leaf = [&](u32 done_li) -> u32 {
+    if (!dyn) return done_li == kNone ? blockIdx.x * groups + g : cnt;  // one leaf per group
+    u32 li = 0;
+    if (tid == 0) s_li[g] = atomicAdd(&c.status->cur_leaf[cls], 1u);
+    S::sync();
+    li = s_li[g];
+    S::sync();
+    return li;
+  };
+  for (u32 li = next_leaf(kNone); li < cnt; li = next_leaf(li)) {
     const Leaf L = c.leaves_cur[cls][li];
     const Inst I = c.inst[L.inst];
     E *s = smem + g * S::SMEM;
@@ -347,10 +357,20 @@ __global__ void __launch_bounds__(T, (T <= 512 && sizeof(typename KT<DT>::elem_t
   E *s = reinterpret_cast<E *>(smem_raw);
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
-  const u32 cnt = count != kDev ? count : min(c.cnt_cur->leaves[cls], c.leaf_cap[cls]);
+  const bool dyn = count == kDev;  // a fixed-size grid: every cluster takes the next leaf
+  const u32 cnt = dyn ? min(c.cnt_cur->leaves[cls], c.leaf_cap[cls]) : count;
   const int tid = threadIdx.x;
   u32 *nl = reinterpret_cast<u32 *>(smem_raw + leaf_sort_bytes<DT, T, R, false>());  // K::lossy only: this part's NaNs
-  for (u32 li = blockIdx.x / G; li < cnt; li += gridDim.x / G) {  // the whole cluster
+  __shared__ u32 s_li;
+  auto next_leaf = [&](u32 done_li) -> u32 {
+    if (!dyn) return done_li == kNone ? blockIdx.x / G : cnt;  // one leaf per cluster
+    if (rank == 0 && tid == 0) s_li = atomicAdd(&c.status->cur_leaf[cls], 1u);
+    cl.sync();
+    const u32 li = *cl.map_shared_rank(&s_li, 0);
+    cl.sync();  // read everywhere before rank 0 takes the next
+    return li;
+  };
+  for (u32 li = next_leaf(kNone); li < cnt; li = next_leaf(li)) {  // the whole cluster
     const Leaf L = c.leaves_cur[cls][li];
     const Inst I = c.inst[L.inst];
     const u64 off = L.off + (u64)rank * CS::NC;
@@ -1436,7 +1456,7 @@ static __global__ void k_round_begin(const Ctx *__restrict__ cp) {
   u32 *z = reinterpret_cast<u32 *>(c.cnt_nxt);
   for (u32 i = threadIdx.x; i < nc; i += blockDim.x) z[i] = 0;
   u32 *cur = &c.status->cur_count;
-  if (threadIdx.x < 7) cur[threadIdx.x] = 0;
+  if (threadIdx.x < 7 + kLeafClasses) cur[threadIdx.x] = 0;
 }
 
 // Totals of a graph-launched run (a host-driven run counts on the host).

@@ -253,9 +253,10 @@ struct Status {
   // per-round work totals written by the plan step
   u32 units, tiles, srows, echunks;
   u64 meta_words;
-  // persistent-kernel work cursors (zeroed every round, with fix_count)
+  // persistent-kernel work cursors (zeroed every round, with fix_count and
+  // the leaf cursors of graph-launched rounds)
   u32 cur_count, cur_scan, cur_skew, cur_expand, cur_ebkt, cur_fix, fix_count;
-  u32 pad;
+  u32 cur_leaf[kLeafClasses];
 };
 
 // A trace record, one per recursing node (written when its pivots are chosen).
