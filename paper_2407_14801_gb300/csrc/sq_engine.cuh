@@ -247,7 +247,7 @@ struct Engine {
   static cudaError_t issue_round(Launcher &L, const Ctx *cp, const Counters *hc, const RoundArgs &A) {
     const cudaStream_t st = L.st;
     const int nsm = A.nsm;
-    const int grid_count = nsm * 2, grid_scan = nsm * 8, grid_skew = nsm * 5, grid_skew_tags = nsm * 4,
+    const int grid_count = nsm * 2, grid_scan = nsm * 8, grid_skew = nsm * 5, grid_skew_tags = nsm * (32 / SQ_SKEW_WARPS),
               grid_expand = nsm * 4;
     cudaError_t e;
 #define SQ_TRY(x)                      \
@@ -303,9 +303,10 @@ struct Engine {
       const size_t smem_skew = sizeof(SkewSmem<DT, SKEW_CAP>);
       L.begin(KF_SKEW);
       if (A.tags) {  // every instance has tag scratch: a counting sort by the count's tags
-        const size_t smem_tags = sizeof(SkewTagSmem<DT, SKEW_CAP>);
-        SQ_TRY(set_smem(k_skew_tags<DT, SKEW_CAP>, smem_tags));
-        k_skew_tags<DT, SKEW_CAP><<<grid_skew_tags, 256, smem_tags, st>>>(cp, ready);
+        constexpr int CAP_T = 256 * SQ_SKEW_WARPS;  // 256 elements a warp per chunk
+        const size_t smem_tags = sizeof(SkewTagSmem<DT, CAP_T>);
+        SQ_TRY(set_smem(k_skew_tags<DT, CAP_T>, smem_tags));
+        k_skew_tags<DT, CAP_T><<<grid_skew_tags, 32 * SQ_SKEW_WARPS, smem_tags, st>>>(cp, ready);
       } else {
         SQ_TRY(set_smem(k_skew<DT, SKEW_CAP, false>, smem_skew));
         k_skew<DT, SKEW_CAP, false><<<grid_skew, 256, smem_skew, st>>>(cp, ready);

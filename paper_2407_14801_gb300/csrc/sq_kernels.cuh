@@ -285,6 +285,7 @@ __global__ void __launch_bounds__(WARP ? 256 : T, kLeafMinBlocks<DT, T, WARP>())
   const bool dyn = count == kDev;  // a fixed-size grid: every group takes the next leaf
   const u32 cnt = dyn ? min(c.cnt_cur->leaves[cls], c.leaf_cap[cls]) : count;
   __shared__ u32 s_li[groups];
+  __shared__ u32 s_pre[groups][S::kPreWords];
   auto next_leaf = [&](u32 done_li) -> u32 {
     if (!dyn) return done_li == kNone ? blockIdx.x * groups + g : cnt;  // one leaf per group
     u32 li = 0;
@@ -323,10 +324,16 @@ __global__ void __launch_bounds__(WARP ? 256 : T, kLeafMinBlocks<DT, T, WARP>())
         continue;
       }
     }
-    S::sort(x, s, tid);
-    S::store(x, s, tid, ok, ov, L.n);
+    u32 rot = 0;
+    const int pre = S::presorted(x, s, tid, L.n, s_pre[g], rot);
+    if (pre == 0) S::sort(x, s, tid);
+    if (pre != 1 || out) {  // (a sorted leaf in place is left as it is)
+      const int n = (int)L.n, r = pre == 3 ? (int)rot : 0;
+      const bool rev = pre == 2;
+      S::store_mapped(x, s, tid, ok, ov, L.n, [&](int i) { return rev ? n - 1 - i : (i >= r ? i - r : i + n - r); });
+    }
     if constexpr (K::lossy) {
-      if (nn) {
+      if (nn && (pre != 1 || out)) {  // (a sorted leaf left in place kept its bits)
         for (u32 i = tid; i < nn; i += T) ok[L.n - nn + nan_rank(nl, nn, nl[1 + i], i)] = (key_t)nl[1 + kNanCap + i];
         S::sync();
       }
@@ -362,6 +369,7 @@ __global__ void __launch_bounds__(T, (T <= 512 && sizeof(typename KT<DT>::elem_t
   const int tid = threadIdx.x;
   u32 *nl = reinterpret_cast<u32 *>(smem_raw + leaf_sort_bytes<DT, T, R, false>());  // K::lossy only: this part's NaNs
   __shared__ u32 s_li;
+  __shared__ typename CS::PreW s_pre;
   auto next_leaf = [&](u32 done_li) -> u32 {
     if (!dyn) return done_li == kNone ? blockIdx.x / G : cnt;  // one leaf per cluster
     if (rank == 0 && tid == 0) s_li = atomicAdd(&c.status->cur_leaf[cls], 1u);
@@ -409,11 +417,25 @@ __global__ void __launch_bounds__(T, (T <= 512 && sizeof(typename KT<DT>::elem_t
         continue;
       }
     }
-    CS::sort(x, s, tid, (int)L.n);
-    S::store(x, s, tid, ok + q0, ov + q0, nr);
+    u32 rot = 0;
+    const int pre = CS::presorted(x, s, tid, L.n, &s_pre, rot);
+    if (pre <= 1) {
+      if (pre == 0) CS::sort(x, s, tid, (int)L.n);
+      if (pre == 0 || out) S::store(x, s, tid, ok + q0, ov + q0, nr);  // a sorted leaf in place stays
+    } else {  // reversed or rotated: every element straight to its place
+#pragma unroll
+      for (int k = 0; k < R; k++) {
+        const u32 i = q0 + (u32)(tid * R + k);
+        if (i < L.n) {
+          const u32 to = pre == 2 ? L.n - 1 - i : (i >= rot ? i - rot : i + L.n - rot);
+          ok[to] = K::key(x[k]);
+          ov[to] = K::val(x[k]);
+        }
+      }
+    }
     cl.sync();
     if constexpr (K::lossy) {
-      if (total) {  // the leaf's NaNs end it, in val order (then by part, entry)
+      if (total && (pre != 1 || out)) {  // the leaf's NaNs end it, in val order (then by part, entry)
         for (u32 i = tid; i < nn; i += T) {
           const u32 v = nl[1 + i];
           u32 r = 0;
@@ -1105,10 +1127,13 @@ __global__ void __launch_bounds__(256) k_skew(const Ctx *__restrict__ cp, u32 re
 // __match_any_sync; a (tag, warp) counter kept by the group's lowest lane),
 // one scan over the (tag, warp) counters gives every element its slot in
 // shared memory, and the chunk leaves with one coalesced run per bucket.
+#ifndef SQ_SKEW_WARPS
+#define SQ_SKEW_WARPS 4  // warps of a SkewTranspose CTA (each ranks 256 elements of a chunk)
+#endif
 template <int DT, int CAP>
 struct SkewTagSmem {
   typedef typename KT<DT>::elem_t E;
-  static constexpr int NW = 8;  // warps of a CTA
+  static constexpr int NW = SQ_SKEW_WARPS;  // warps of a CTA
   E out_e[CAP];
   uint8_t out_j[CAP];
   u32 cnt[kSkewBkts * (NW + 1)];  // (tag, warp), tag-major, padded rows
@@ -1118,7 +1143,8 @@ struct SkewTagSmem {
 };
 
 template <int DT, int CAP>
-__global__ void __launch_bounds__(256, 4) k_skew_tags(const Ctx *__restrict__ cp, u32 ready_count) {
+__global__ void __launch_bounds__(32 * SQ_SKEW_WARPS, 32 / SQ_SKEW_WARPS) k_skew_tags(const Ctx *__restrict__ cp,
+                                                                                   u32 ready_count) {
   const Ctx &c = *cp;
   if (ready_count == kDev) ready_count = min(c.cnt_cur->ready, c.ready_cap);
   typedef KT<DT> K;
@@ -1182,7 +1208,7 @@ __global__ void __launch_bounds__(256, 4) k_skew_tags(const Ctx *__restrict__ cp
     const uint8_t *tg = I.tags + nd.off;
     key_t *ak = (key_t *)I.keys + nd.off;
     u32 *av = I.vals + nd.off;
-    for (int i = tid; i < kSkewBkts * (NW + 1); i += 256) sm.cnt[i] = 0;
+    for (int i = tid; i < kSkewBkts * (NW + 1); i += 32 * NW) sm.cnt[i] = 0;
     __syncthreads();
     for (u32 cs = 0; cs < S; cs += CAP) {
       const u32 L = min((u32)CAP, S - cs);
@@ -1266,7 +1292,7 @@ __global__ void __launch_bounds__(256, 4) k_skew_tags(const Ctx *__restrict__ cp
       }
       __syncthreads();
       // one coalesced run per bucket; the counters are free for the next chunk
-      for (u32 s2 = tid; s2 < L; s2 += 256) {
+      for (u32 s2 = tid; s2 < L; s2 += 32 * NW) {
         const u32 dest = sm.adj[sm.out_j[s2]] + s2;
         const E e = sm.out_e[s2];
         if (dest < nd.n) {
@@ -1276,7 +1302,7 @@ __global__ void __launch_bounds__(256, 4) k_skew_tags(const Ctx *__restrict__ cp
           atomicOr(&c.status->error, ERRB_SIZES);
         }
       }
-      for (int i = tid; i < kSkewBkts * (NW + 1); i += 256) sm.cnt[i] = 0;
+      for (int i = tid; i < kSkewBkts * (NW + 1); i += 32 * NW) sm.cnt[i] = 0;
       __syncthreads();
     }
   }

@@ -198,8 +198,17 @@ struct Sorter {
 
   // Stores the first n sorted elements (coalesced, through shared memory).
   __device__ static void store(E (&x)[R], E *s, int tid, typename K::key_t *keys, u32 *vals, u32 n) {
+    store_mapped(x, s, tid, keys, vals, n, [](int i) { return i; });
+  }
+
+  // The same, position i of x's blocked order going to position to(i).
+  template <class Map>
+  __device__ static void store_mapped(E (&x)[R], E *s, int tid, typename K::key_t *keys, u32 *vals, u32 n, Map to) {
 #pragma unroll
-    for (int k = 0; k < R; k++) s[px(tid * R + k)] = x[k];
+    for (int k = 0; k < R; k++) {
+      const int i = tid * R + k;
+      s[px((u32)i < n ? to(i) : i)] = x[k];
+    }
     sync();
 #pragma unroll
     for (int k = 0; k < R; k++) {
@@ -211,6 +220,54 @@ struct Sorter {
       }
     }
     sync();
+  }
+
+  // Presorted input (what an insertion-sort base case finds cheaply): x
+  // holds positions [tid*R, tid*R + R) as loaded, s all N.  Counts the descents x[i] > x[i+1]
+  // among the first n; returns 1 if there are none (sorted), 2 if every
+  // step descends (reversed), 3 if there is exactly one, at p - 1, and
+  // x[n-1] <= x[0] (two sorted runs in swapped order), else 0.  w:
+  // kPreWords of shared memory (one pair per warp; free again once any
+  // later barrier of the group has passed).
+  static constexpr int kPreWords = WARP ? 1 : 2 * (T / 32);
+  __device__ static void descents(const E (&x)[R], const E *s, int tid, u32 n, u32 &d, u32 &first) {
+    d = 0;
+    first = 0xffffffffu;
+#pragma unroll
+    for (int k = 0; k < R; k++) {  // x holds positions tid*R + k; the next thread's first is in s
+      const u32 i = (u32)(tid * R + k);
+      if (i + 1 < n) {
+        const E nx = k + 1 < R ? x[k + 1] : s[px(tid * R + R)];
+        if (K::lt(nx, x[k])) {
+          first = d ? first : i;
+          ++d;
+        }
+      }
+    }
+    d = __reduce_add_sync(0xffffffffu, d);
+    first = __reduce_min_sync(0xffffffffu, first);
+  }
+  __device__ static int presorted(E (&x)[R], E *s, int tid, u32 n, u32 *w, u32 &p) {
+    // (s is read only before the barrier: once past it, other threads may
+    // already be writing the sorted or moved leaf into s)
+    const bool wrap = n >= 2 && !K::lt(s[px(0)], s[px((int)n - 1)]);
+    u32 d, first;
+    descents(x, s, tid, n, d, first);
+    if (!WARP) {
+      if ((tid & 31) == 0) {
+        w[2 * (tid >> 5)] = d;
+        w[2 * (tid >> 5) + 1] = first;
+      }
+      __syncthreads();
+      const int l = tid & 31;  // lane l adds warp l's pair
+      d = __reduce_add_sync(0xffffffffu, l < T / 32 ? w[2 * l] : 0u);
+      first = __reduce_min_sync(0xffffffffu, l < T / 32 ? w[2 * l + 1] : 0xffffffffu);
+    }
+    p = first + 1;
+    if (n < 2 || d == 0) return 1;
+    if (d == n - 1) return 2;
+    if (d == 1 && wrap) return 3;
+    return 0;
   }
 };
 
@@ -225,6 +282,65 @@ struct ClusterSorter {
   typedef typename K::elem_t E;
   static constexpr int NC = T * R;  // elements per CTA
   static constexpr int N = NC * G;
+
+  // Sorter::presorted over the whole leaf of n elements held by the
+  // cluster (this CTA's part as loaded in s).  Each CTA counts the descents
+  // inside its part and publishes them with its first and last element in
+  // w; after one cluster barrier every CTA adds the descents between parts
+  // and returns the same answer.  w is read by the other CTAs until the
+  // cluster's next barrier.
+  struct PreW {
+    E head, tail;
+    u32 wd[S::kPreWords];
+    u32 d, first;
+  };
+  __device__ static int presorted(E (&x)[R], E *s, int tid, u32 n, PreW *w, u32 &p) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const u32 q0 = (u32)rank * NC;
+    const u32 nr = n > q0 ? min((u32)NC, n - q0) : 0u;
+    u32 d, first;
+    S::descents(x, s, tid, nr, d, first);
+    if ((tid & 31) == 0) {
+      w->wd[2 * (tid >> 5)] = d;
+      w->wd[2 * (tid >> 5) + 1] = first;
+    }
+    __syncthreads();
+    if (tid < 32) {  // lane l adds warp l's pair
+      d = __reduce_add_sync(0xffffffffu, tid < T / 32 ? w->wd[2 * tid] : 0u);
+      first = __reduce_min_sync(0xffffffffu, tid < T / 32 ? w->wd[2 * tid + 1] : 0xffffffffu);
+    }
+    if (tid == 0) {
+      w->d = d;
+      w->first = first == 0xffffffffu ? first : q0 + first;
+      if (nr) {
+        w->head = s[S::px(0)];
+        w->tail = s[S::px((int)nr - 1)];
+      }
+    }
+    cl.sync();
+    u32 tot = 0, fst = 0xffffffffu;
+    E head = E(), tail = E();
+    for (int r = 0; r < G && (u32)r * NC < n; r++) {
+      const PreW *pw = cl.map_shared_rank(w, r);
+      const E h = pw->head;
+      tot += pw->d;
+      fst = min(fst, pw->first);
+      if (r == 0)
+        head = h;
+      else if (K::lt(h, tail)) {  // the descent between part r-1 and part r
+        ++tot;
+        fst = min(fst, (u32)r * NC - 1);
+      }
+      tail = pw->tail;
+    }
+    p = fst + 1;
+    if (n < 2 || tot == 0) return 1;
+    if (tot == n - 1) return 2;
+    if (tot == 1 && !K::lt(head, tail)) return 3;
+    return 0;
+  }
 
   // n: valid elements of the whole leaf (the rest top(), as left by
   // S::load).

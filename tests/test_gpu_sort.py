@@ -190,3 +190,63 @@ def test_f32_leaf_nan_bits_restored(sq, n):
         check_against_oracle(sq, keys, vals, "f32", seed=nan_count, cutoff=65536)
         if n > 2048:  # also as a recursion whose leaves carry a few NaNs each
             check_against_oracle(sq, keys, vals, "f32", seed=nan_count, cutoff=2048)
+
+
+def _presorted_cases(n, rng):
+    """Leaves the adaptive base case takes without sorting (sorted, strictly
+    reversed, two sorted runs swapped) and near misses it must sort."""
+    base = np.sort(rng.integers(0, 1 << 32, size=n, dtype=np.uint64).astype(np.uint32))
+    iota = W.iota(n)
+    yield "sorted", base.copy(), iota
+    yield "reversed", base[::-1].copy(), iota
+    yield "equal keys, payload ascending", np.full(n, 5, np.uint32), iota
+    yield "equal keys, payload descending", np.full(n, 5, np.uint32), iota[::-1].copy()
+    if n >= 2:
+        for p in sorted({1, n // 3, n - 1}):
+            yield f"rotated at {p}", np.roll(base, -p).copy(), np.roll(iota, -p).copy()
+        # the two runs meet at an equal key: the payloads decide
+        k = np.sort(rng.integers(0, 50, size=n, dtype=np.uint32))
+        k[0] = k[-1] = 50
+        k = np.sort(k)
+        yield "rotated, equal key at the seam", np.roll(k, -(n // 2)).copy(), np.roll(iota, -(n // 2)).copy()
+    if n >= 3:
+        sw = base.copy()
+        sw[[n // 2, n // 2 - 1]] = sw[[n // 2 - 1, n // 2]]
+        yield "sorted but one swap", sw, iota
+        rv = base[::-1].copy()
+        rv[n // 2] = rv[n // 2 - 1]  # a tie breaks the strict descent: sorted the usual way
+        yield "reversed with a tie", rv, iota
+        two = np.concatenate([base[: n // 2][::-1], base[n // 2:]])
+        yield "two descents at the seam", np.roll(two, 1).copy(), iota
+
+
+@pytest.mark.parametrize("n", [2, 3, 40, 64, 400, 512, 2000, 2048, 8000, 8192, 16000, 24577, 40000, 57345, 65536])
+def test_presorted_leaves(sq, n):
+    """The leaf kernels detect sorted, reversed and rotated input and only
+    move it; every other input is sorted.  Each case against the oracle, as
+    one leaf (the whole input, sorted in place) and, for the larger sizes,
+    as a recursion whose columns and buckets are leaves."""
+    rng = np.random.default_rng(n)
+    for name, keys, vals in _presorted_cases(n, rng):
+        check_against_oracle(sq, keys, vals, "u32", seed=n, cutoff=65536)
+        if n > 8192:
+            check_against_oracle(sq, keys, vals, "u32", seed=n, cutoff=4096)
+
+
+@pytest.mark.parametrize("n", [100, 3000, 20000, 65536])
+def test_presorted_leaves_wide_keys(sq, n):
+    """The same for uint64 keys and for float32 keys with NaNs (which sort
+    last and keep their bits)."""
+    rng = np.random.default_rng(n + 1)
+    base = np.sort(rng.integers(0, 1 << 64, size=n, dtype=np.uint64))
+    iota = W.iota(n)
+    for keys, vals in ((base, iota), (base[::-1].copy(), iota), (np.roll(base, -(n // 4)), np.roll(iota, -(n // 4)))):
+        check_against_oracle(sq, keys.copy(), vals.copy(), "u64", seed=2, cutoff=65536)
+    f = np.sort(W.normal_f32(n, n, p_inf=0.01, p_negzero=0.01, p_nan=0.0))
+    bits = f.view(np.uint32)
+    nn = max(1, n // 100)
+    bits[-nn:] = np.uint32(0x7FC00000) | rng.integers(0, 1 << 22, size=nn, dtype=np.uint32)
+    for keys, vals in ((f, iota), (f[::-1].copy(), iota[::-1].copy()), (np.roll(f, -(n // 3)), np.roll(iota, -(n // 3)))):
+        check_against_oracle(sq, keys.copy(), vals.copy(), "f32", seed=3, cutoff=65536)
+        if n > 8192:
+            check_against_oracle(sq, keys.copy(), vals.copy(), "f32", seed=3, cutoff=2048)
