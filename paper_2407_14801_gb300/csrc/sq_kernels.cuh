@@ -269,6 +269,63 @@ __host__ __device__ constexpr size_t leaf_sort_bytes() {
   return (size_t)(WARP ? 8 : 1) * Sorter<KT<DT>, T, R, WARP>::SMEM * sizeof(typename KT<DT>::elem_t);
 }
 
+// A leaf whose ascending runs descend (Sorter::runs) is moved run by run:
+// every output position, in coalesced order, takes its element from the
+// loaded copy in s.  Returns false (nothing written) if the runs do not
+// descend.  Kept out of line: the test needs registers that the merge sort,
+// the common path, must not lose.
+template <class S>
+__device__ __noinline__ bool leaf_runs(const typename S::E *s, int tid, u32 n, u32 *w, typename S::RunInfo *ri,
+                                       typename S::K::key_t *ok, u32 *ov) {
+  typedef typename S::K K;
+  if (!S::runs(s, tid, n, w, ri)) return false;
+  constexpr int T = S::N / S::R;
+#pragma unroll 4
+  for (int k = 0; k < S::R; k++) {
+    const u32 o = (u32)(k * T + tid);
+    if (o < n) {
+      const u32 j = n - 1u - o;
+      const typename S::E e = s[S::px((int)S::run_source(j, ri[j / S::R], (int)(j % S::R)))];
+      ok[o] = K::key(e);
+      ov[o] = K::val(e);
+    }
+  }
+  return true;
+}
+// The same for a cluster's leaf (pre: 2 reversed, 3 rotated at rot, 4 runs
+// to be tested), every CTA writing its part of the output from the parts in
+// the cluster's shared memories.
+template <class CS>
+__device__ __noinline__ bool leaf_move_cluster(const typename CS::E *s, int tid, u32 n, int pre, u32 rot,
+                                               typename CS::PreW *w, typename CS::S::K::key_t *ok, u32 *ov) {
+  typedef typename CS::S S;
+  typedef typename S::K K;
+  constexpr int T = S::N / S::R, R = S::R, NC = CS::NC;
+  if (pre == 4 && !CS::runs(s, tid, n, w)) return false;
+  cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+  const u32 q0 = (u32)cl.block_rank() * NC;
+#pragma unroll 4
+  for (int k = 0; k < R; k++) {
+    const u32 o = q0 + (u32)(k * T + tid);
+    if (o < n) {
+      u32 src;
+      if (pre == 2) {
+        src = n - 1u - o;
+      } else if (pre == 3) {
+        src = o + rot < n ? o + rot : o + rot - n;
+      } else {
+        const u32 j = n - 1u - o;
+        const typename S::RunInfo r = cl.map_shared_rank(w, (int)(j / NC))->ri[(j % NC) / R];
+        src = S::run_source(j, r, (int)(j % R));
+      }
+      const typename S::E e = *cl.map_shared_rank(s + S::px((int)(src % NC)), (int)(src / NC));
+      ok[o] = K::key(e);
+      ov[o] = K::val(e);
+    }
+  }
+  return true;
+}
+
 template <int DT, int T, int R, bool WARP>
 __global__ void __launch_bounds__(WARP ? 256 : T, kLeafMinBlocks<DT, T, WARP>()) k_leaf(const Ctx *__restrict__ cp, int cls, u32 count) {
   const Ctx &c = *cp;
@@ -286,6 +343,8 @@ __global__ void __launch_bounds__(WARP ? 256 : T, kLeafMinBlocks<DT, T, WARP>())
   const u32 cnt = dyn ? min(c.cnt_cur->leaves[cls], c.leaf_cap[cls]) : count;
   __shared__ u32 s_li[groups];
   __shared__ u32 s_pre[groups][S::kPreWords];
+  __shared__ u32 s_run[groups][S::kRunWords];
+  __shared__ typename S::RunInfo s_ri[groups][T];
   auto next_leaf = [&](u32 done_li) -> u32 {
     if (!dyn) return done_li == kNone ? blockIdx.x * groups + g : cnt;  // one leaf per group
     u32 li = 0;
@@ -325,9 +384,15 @@ __global__ void __launch_bounds__(WARP ? 256 : T, kLeafMinBlocks<DT, T, WARP>())
       }
     }
     u32 rot = 0;
-    const int pre = S::presorted(x, s, tid, L.n, s_pre[g], rot);
+    int pre = S::presorted(x, s, tid, L.n, s_pre[g], rot);
+    if (pre == 4) {  // runs in descending order: every element straight to its place, else sorted
+      if (!leaf_runs<S>(s, tid, L.n, s_run[g], s_ri[g], ok, ov)) pre = 0;
+#pragma unroll
+      for (int k = 0; k < R; k++) x[k] = s[S::px(tid * R + k)];
+      S::sync();  // (the moved leaf is written before its NaNs get their bits back)
+    }
     if (pre == 0) S::sort(x, s, tid);
-    if (pre != 1 || out) {  // (a sorted leaf in place is left as it is)
+    if (pre < 4 && (pre != 1 || out)) {  // (a sorted leaf in place is left as it is)
       const int n = (int)L.n, r = pre == 3 ? (int)rot : 0;
       const bool rev = pre == 2;
       S::store_mapped(x, s, tid, ok, ov, L.n, [&](int i) { return rev ? n - 1 - i : (i >= r ? i - r : i + n - r); });
@@ -418,22 +483,17 @@ __global__ void __launch_bounds__(T, (T <= 512 && sizeof(typename KT<DT>::elem_t
       }
     }
     u32 rot = 0;
-    const int pre = CS::presorted(x, s, tid, L.n, &s_pre, rot);
+    int pre = CS::presorted(x, s, tid, L.n, &s_pre, rot);
+    if (pre >= 2) {  // reversed, rotated, or runs in descending order (if they pass the test): moved
+      if (!leaf_move_cluster<CS>(s, tid, L.n, pre, rot, &s_pre, ok, ov)) pre = 0;
+#pragma unroll
+      for (int k = 0; k < R; k++) x[k] = s[S::px(tid * R + k)];
+    }
     if (pre <= 1) {
       if (pre == 0) CS::sort(x, s, tid, (int)L.n);
       if (pre == 0 || out) S::store(x, s, tid, ok + q0, ov + q0, nr);  // a sorted leaf in place stays
-    } else {  // reversed or rotated: every element straight to its place
-#pragma unroll
-      for (int k = 0; k < R; k++) {
-        const u32 i = q0 + (u32)(tid * R + k);
-        if (i < L.n) {
-          const u32 to = pre == 2 ? L.n - 1 - i : (i >= rot ? i - rot : i + L.n - rot);
-          ok[to] = K::key(x[k]);
-          ov[to] = K::val(x[k]);
-        }
-      }
     }
-    cl.sync();
+    cl.sync();  // (also: no part changes before every CTA has read what it moves)
     if constexpr (K::lossy) {
       if (total && (pre != 1 || out)) {  // the leaf's NaNs end it, in val order (then by part, entry)
         for (u32 i = tid; i < nn; i += T) {

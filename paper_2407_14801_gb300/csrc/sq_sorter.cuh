@@ -96,8 +96,10 @@ __device__ __forceinline__ void serial_merge(typename K::elem_t (&x)[R], int ai,
 }
 
 // T threads (T == 32 and WARP: one warp of a larger CTA), R elements each.
-template <class K, int T, int R, bool WARP>
+template <class K_, int T, int R_, bool WARP>
 struct Sorter {
+  typedef K_ K;
+  static constexpr int R = R_;
   typedef typename K::elem_t E;
   static constexpr int N = T * R;
   static constexpr int SMEM = N + N / R;  // padded element slots
@@ -223,13 +225,24 @@ struct Sorter {
   }
 
   // Presorted input (what an insertion-sort base case finds cheaply): x
-  // holds positions [tid*R, tid*R + R) as loaded, s all N.  Counts the descents x[i] > x[i+1]
-  // among the first n; returns 1 if there are none (sorted), 2 if every
-  // step descends (reversed), 3 if there is exactly one, at p - 1, and
-  // x[n-1] <= x[0] (two sorted runs in swapped order), else 0.  w:
-  // kPreWords of shared memory (one pair per warp; free again once any
-  // later barrier of the group has passed).
+  // holds positions [tid*R, tid*R + R) as loaded, s all N.  Counts the
+  // descents x[i] > x[i+1] among the first n; returns 1 if there are none
+  // (sorted), 2 if every step descends (reversed), 3 if there is exactly
+  // one, at p - 1, and x[n-1] <= x[0] (two sorted runs in swapped order),
+  // 4 if there are few (at most kFewRuns) or almost n (at least n - n/8):
+  // worth the runs test below; else 0.  w: kPreWords of shared memory (one
+  // pair per warp; free again once any later barrier of the group has
+  // passed).
   static constexpr int kPreWords = WARP ? 1 : 2 * (T / 32);
+  static constexpr u32 kFewRuns = 32;
+  static_assert(R < 32, "a thread's descents fit one mask word");
+  __device__ __forceinline__ static int classify(u32 n, u32 d, bool wrap) {
+    if (n < 2 || d == 0) return 1;
+    if (d == n - 1) return 2;
+    if (d == 1 && wrap) return 3;
+    if (d <= kFewRuns || d >= n - n / 8) return 4;
+    return 0;
+  }
   __device__ static void descents(const E (&x)[R], const E *s, int tid, u32 n, u32 &d, u32 &first) {
     d = 0;
     first = 0xffffffffu;
@@ -264,10 +277,122 @@ struct Sorter {
       first = __reduce_min_sync(0xffffffffu, l < T / 32 ? w[2 * l + 1] : 0xffffffffu);
     }
     p = first + 1;
-    if (n < 2 || d == 0) return 1;
-    if (d == n - 1) return 2;
-    if (d == 1 && wrap) return 3;
-    return 0;
+    return classify(n, d, wrap);
+  }
+
+  // Runs.  A leaf's ascending runs are the stretches between its descents.
+  // When each run lies entirely below the run before it (a reversed input
+  // with ties, a few sorted runs swapped), the leaf is sorted by putting the
+  // runs in reverse order: the run [b, e) holding element i sends it to
+  // n - e + (i - b).  A thread describes its runs by the mask of its
+  // descents (bit k: one at base + k) and the bounds of the runs that cross
+  // its ends (pre: the start of the run holding its first element; suf: the
+  // end of the run holding its last).
+  // (The runs test reads the loaded leaf from s only, so that x is free
+  // meanwhile.)
+  __device__ static u32 desc_mask(const E *s, int tid, u32 n) {
+    u32 m = 0;
+    E cur = s[px(tid * R)];
+#pragma unroll
+    for (int k = 0; k < R; k++) {
+      const u32 i = (u32)(tid * R + k);
+      if (i + 1 < n) {
+        const E nx = s[px(tid * R + k + 1)];
+        if (K::lt(nx, cur)) m |= 1u << k;
+        cur = nx;
+      }
+    }
+    return m;
+  }
+  // b and e of the element at base + k
+  __device__ __forceinline__ static u32 run_b(u32 m, int k, u32 base, u32 pre) {
+    const u32 lb = m & ((1u << k) - 1u);  // the descents before it
+    return lb ? base + 32u - (u32)__clz((int)lb) : pre;
+  }
+  __device__ __forceinline__ static u32 run_e(u32 m, int k, u32 base, u32 suf) {
+    const u32 hb = m & ~((1u << k) - 1u);  // the descents at or after it
+    return hb ? base + (u32)__ffs((int)hb) : suf;
+  }
+  // pre and suf for every thread of the group from the masks: the largest
+  // run start of the earlier threads (lo if none) and the smallest run end
+  // of the later ones (hi if none); tmax and tmin: the group's own largest
+  // run start and smallest run end.  w: kRunWords of shared memory.
+  static constexpr int kRunWords = WARP ? 1 : 2 * (T / 32);
+  __device__ static void run_scan(u32 m, u32 base, int tid, u32 lo, u32 hi, u32 *w, u32 &pre, u32 &suf, u32 &tmax,
+                                  u32 &tmin) {
+    const int lane = tid & 31;
+    u32 a = m ? base + 32u - (u32)__clz((int)m) : lo;  // the start of the thread's last run
+    u32 z = m ? base + (u32)__ffs((int)m) : hi;        // the end of its first run
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u32 ta = __shfl_up_sync(0xffffffffu, a, o);
+      const u32 tz = __shfl_down_sync(0xffffffffu, z, o);
+      if (lane >= o) a = max(a, ta);
+      if (lane + o < 32) z = min(z, tz);
+    }
+    pre = __shfl_up_sync(0xffffffffu, a, 1);
+    suf = __shfl_down_sync(0xffffffffu, z, 1);
+    if (lane == 0) pre = lo;
+    if (lane == 31) suf = hi;
+    tmax = __shfl_sync(0xffffffffu, a, 31);
+    tmin = __shfl_sync(0xffffffffu, z, 0);
+    if (!WARP) {
+      const int wid = tid >> 5;
+      if (lane == 0) {
+        w[wid] = tmax;
+        w[T / 32 + wid] = tmin;
+      }
+      __syncthreads();
+      tmax = lo;
+      tmin = hi;
+#pragma unroll
+      for (int j = 0; j < T / 32; j++) {
+        const u32 wa = w[j], wz = w[T / 32 + j];
+        if (j < wid) pre = max(pre, wa);
+        if (j > wid) suf = min(suf, wz);
+        tmax = max(tmax, wa);
+        tmin = min(tmin, wz);
+      }
+    }
+  }
+  // This thread's share of the test that the runs in reverse order are
+  // sorted: at each of its descents d, the run after it, [d+1, e), must end
+  // no higher than the run before it, [b, d+1), starts (x[e-1] <= x[b]).
+  // at(p): the element at leaf position p.
+  template <class At>
+  __device__ static bool runs_descend(u32 m, u32 base, u32 pre, u32 suf, At at) {
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < R; k++)
+      if (m >> k & 1u) {
+        const u32 b = run_b(m, k, base, pre), e = run_e(m, k + 1, base, suf);
+        if (K::lt(at(b), at(e - 1))) ok = false;
+      }
+    return ok;
+  }
+  // A thread's runs, kept for the move.
+  struct RunInfo {
+    u32 m, pre, suf;
+  };
+  // The runs test for a group holding the whole leaf; ri[tid] gets this
+  // thread's runs (read by the others after the test's closing barrier).
+  __device__ static bool runs(const E *s, int tid, u32 n, u32 *w, RunInfo *ri) {
+    const u32 m = desc_mask(s, tid, n);
+    const u32 base = (u32)(tid * R);
+    u32 pre, suf, tmax, tmin;
+    run_scan(m, base, tid, 0u, n, w, pre, suf, tmax, tmin);
+    ri[tid] = RunInfo{m, pre, suf};
+    const bool ok = runs_descend(m, base, pre, suf, [&](u32 p) { return s[px((int)p)]; });
+    return WARP ? __all_sync(0xffffffffu, ok) : __syncthreads_and(ok);
+  }
+  // Where the element at output position o comes from when the runs are
+  // put in reverse order: the input run [b, e) fills the outputs
+  // [n - e, n - b), so with j = n - 1 - o (which lies in that run)
+  // the source is b + e - 1 - j.  r: the runs of the thread holding j,
+  // kj: j's index within that thread.
+  __device__ __forceinline__ static u32 run_source(u32 j, const RunInfo &r, int kj) {
+    const u32 base = j - (u32)kj;
+    return run_b(r.m, kj, base, r.pre) + run_e(r.m, kj, base, r.suf) - 1u - j;
   }
 };
 
@@ -293,6 +418,9 @@ struct ClusterSorter {
     E head, tail;
     u32 wd[S::kPreWords];
     u32 d, first;
+    u32 wr[S::kRunWords];  // the runs test (written after the count has been read everywhere)
+    u32 rmax, rmin, rok;
+    typename S::RunInfo ri[T];
   };
   __device__ static int presorted(E (&x)[R], E *s, int tid, u32 n, PreW *w, u32 &p) {
     namespace cg = cooperative_groups;
@@ -336,10 +464,42 @@ struct ClusterSorter {
       tail = pw->tail;
     }
     p = fst + 1;
-    if (n < 2 || tot == 0) return 1;
-    if (tot == n - 1) return 2;
-    if (tot == 1 && !K::lt(head, tail)) return 3;
-    return 0;
+    return S::classify(n, tot, !K::lt(head, tail));
+  }
+
+  // Sorter::runs over the whole leaf held by the cluster, after presorted
+  // (whose w it extends, w->ri included); every CTA returns the same answer.
+  __device__ static bool runs(const E *s, int tid, u32 n, PreW *w) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const u32 q0 = (u32)rank * NC;
+    const u32 nr = n > q0 ? min((u32)NC, n - q0) : 0u;
+    u32 m = S::desc_mask(s, tid, nr);
+    if (tid == T - 1 && q0 + NC < n && K::lt(cl.map_shared_rank(w, rank + 1)->head, s[S::px(NC - 1)]))
+      m |= 1u << (R - 1);  // the descent into the next part
+    const u32 base = q0 + (u32)(tid * R);
+    u32 pre, suf, tmax, tmin;
+    S::run_scan(m, base, tid, 0u, n, w->wr, pre, suf, tmax, tmin);
+    if (tid == 0) {
+      w->rmax = tmax;
+      w->rmin = tmin;
+    }
+    cl.sync();
+    for (int r = 0; r < G && (u32)r * NC < n; r++) {
+      const PreW *pw = cl.map_shared_rank(w, r);
+      if (r < rank) pre = max(pre, pw->rmax);
+      if (r > rank) suf = min(suf, pw->rmin);
+    }
+    w->ri[tid] = typename S::RunInfo{m, pre, suf};
+    bool ok = S::runs_descend(m, base, pre, suf, [&](u32 p) {
+      return *cl.map_shared_rank(s + S::px((int)(p % NC)), (int)(p / NC));
+    });
+    ok = __syncthreads_and(ok);
+    if (tid == 0) w->rok = ok;
+    cl.sync();  // (also: every read of a part is done before any part changes)
+    for (int r = 0; r < G && (u32)r * NC < n; r++) ok = ok && cl.map_shared_rank(w, r)->rok;
+    return ok;
   }
 
   // n: valid elements of the whole leaf (the rest top(), as left by

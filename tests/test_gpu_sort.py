@@ -215,9 +215,26 @@ def _presorted_cases(n, rng):
         yield "sorted but one swap", sw, iota
         rv = base[::-1].copy()
         rv[n // 2] = rv[n // 2 - 1]  # a tie breaks the strict descent: sorted the usual way
-        yield "reversed with a tie", rv, iota
+        yield "reversed with one tie", rv, iota
         two = np.concatenate([base[: n // 2][::-1], base[n // 2:]])
         yield "two descents at the seam", np.roll(two, 1).copy(), iota
+        # ascending runs in descending order: moved run by run
+        ties = np.sort(rng.integers(0, 16 * n, size=n, dtype=np.uint32))[::-1].copy()
+        yield "reversed with ties", ties, iota  # about one step in 16 a tie: runs of one or two
+        yield "reversed with many ties", np.sort(rng.integers(0, max(2, n // 8), size=n, dtype=np.uint32))[::-1].copy(), iota
+        for parts in (3, 5, 33):
+            if n >= parts:
+                cuts = np.linspace(0, n, parts + 1).astype(int)
+                runs = [base[cuts[j]:cuts[j + 1]] for j in range(parts)][::-1]
+                yield f"{parts} sorted runs in descending order", np.concatenate(runs), iota
+                shuffled = runs[1:] + runs[:1]  # the same runs, one out of order: sorted the usual way
+                yield f"{parts} sorted runs out of order", np.concatenate(shuffled), iota
+        bad = ties.copy()
+        bad[[0, n - 1]] = bad[[n - 1, 0]]  # first and last swapped: the runs no longer descend
+        yield "reversed with ties, ends swapped", bad, iota
+    if n >= 16384:  # runs meeting exactly at the 8192-element parts of a cluster leaf
+        runs = [base[j:j + 8192] for j in range(0, n - n % 8192, 8192)][::-1]
+        yield "runs at the part boundaries", np.concatenate(runs + [base[n - n % 8192:]][:0]), W.iota(len(runs) * 8192)
 
 
 @pytest.mark.parametrize("n", [2, 3, 40, 64, 400, 512, 2000, 2048, 8000, 8192, 16000, 24577, 40000, 57345, 65536])
@@ -240,13 +257,18 @@ def test_presorted_leaves_wide_keys(sq, n):
     rng = np.random.default_rng(n + 1)
     base = np.sort(rng.integers(0, 1 << 64, size=n, dtype=np.uint64))
     iota = W.iota(n)
-    for keys, vals in ((base, iota), (base[::-1].copy(), iota), (np.roll(base, -(n // 4)), np.roll(iota, -(n // 4)))):
+    tied = np.sort(rng.integers(0, max(2, n // 4), size=n, dtype=np.uint64))[::-1].copy()
+    for keys, vals in ((base, iota), (base[::-1].copy(), iota), (np.roll(base, -(n // 4)), np.roll(iota, -(n // 4))),
+                       (tied, iota)):
         check_against_oracle(sq, keys.copy(), vals.copy(), "u64", seed=2, cutoff=65536)
     f = np.sort(W.normal_f32(n, n, p_inf=0.01, p_negzero=0.01, p_nan=0.0))
     bits = f.view(np.uint32)
     nn = max(1, n // 100)
     bits[-nn:] = np.uint32(0x7FC00000) | rng.integers(0, 1 << 22, size=nn, dtype=np.uint32)
-    for keys, vals in ((f, iota), (f[::-1].copy(), iota[::-1].copy()), (np.roll(f, -(n // 3)), np.roll(iota, -(n // 3)))):
+    ft = np.sort(np.round(W.normal_f32(n, n + 2, p_inf=0.01, p_negzero=0.01, p_nan=0.0) * 4) / 4).astype(np.float32)
+    ft.view(np.uint32)[-nn:] = np.uint32(0xFFC00000) | rng.integers(0, 1 << 22, size=nn, dtype=np.uint32)
+    for keys, vals in ((f, iota), (f[::-1].copy(), iota[::-1].copy()), (np.roll(f, -(n // 3)), np.roll(iota, -(n // 3))),
+                       (ft[::-1].copy(), iota)):
         check_against_oracle(sq, keys.copy(), vals.copy(), "f32", seed=3, cutoff=65536)
         if n > 8192:
             check_against_oracle(sq, keys.copy(), vals.copy(), "f32", seed=3, cutoff=2048)
