@@ -1190,6 +1190,77 @@ __global__ void __launch_bounds__(256) k_skew(const Ctx *__restrict__ cp, u32 re
 #ifndef SQ_SKEW_WARPS
 #define SQ_SKEW_WARPS 4  // warps of a SkewTranspose CTA (each ranks 256 elements of a chunk)
 #endif
+constexpr u32 kSkewBig = 16384;   // tiles this large look for runs of one tag
+constexpr u32 kSkewRunMin = 512;  // the shortest run copied straight
+// Runs of one tag in a big SkewTranspose tile.  Tags ascend within a column
+// segment (the column is sorted), so the stream positions from cs that share
+// its tag form one run: to the end of its column and on through columns of
+// that tag alone (t0/t1: a segment's first and last tag, 0xff if empty), or
+// up to the first other tag in its column, found by a 32-way search (each
+// warp its own, all alike).  Returns the run's end.
+static __device__ __forceinline__ u32 skew_col_of(const u32 *seg_pre, u32 nc, u32 q) {
+  u32 ci = 0;
+#pragma unroll
+  for (u32 st = 16; st > 0; st >>= 1)
+    if (ci + st < nc && seg_pre[ci + st] <= q) ci += st;
+  return ci;
+}
+static __device__ __noinline__ u32 skew_tag_run(const u32 *seg_start, const u32 *seg_pre, const uint8_t *t0,
+                                         const uint8_t *t1, u32 nc, u32 cs, const uint8_t *tg, int lane) {
+  const u32 ci = skew_col_of(seg_pre, nc, cs);
+  const u32 p = seg_start[ci] + (cs - seg_pre[ci]);
+  const u32 tS = tg[p];
+  if (t1[ci] == tS) {
+    u32 cj = ci + 1;
+    while (cj < nc && (t0[cj] == 0xffu || (t0[cj] == tS && t1[cj] == tS))) ++cj;
+    return seg_pre[cj];
+  }
+  u32 lo = p, hi = seg_start[ci] + (seg_pre[ci + 1] - seg_pre[ci]);  // tg[lo] == tS; hi: differs (or the end)
+  while (hi - lo > 1) {
+    const u32 step = (hi - lo + 31) / 32;
+    const u32 pos = lo + step * (u32)(lane + 1);  // lane 31's is at or past hi
+    const u32 ball = __ballot_sync(0xffffffffu, pos >= hi || tg[pos] != tS);
+    const u32 f = (u32)__ffs((int)ball) - 1u;
+    hi = min(hi, lo + step * (f + 1));
+    lo += step * f;
+  }
+  return cs + (hi - p);
+}
+// Copies the run [cs, rend) of the tile's stream to dest d0 on, in order.
+template <class key_t, int NW>
+__device__ __noinline__ void skew_copy_run(const u32 *seg_start, const u32 *seg_pre, u32 nc, u32 cs, u32 rend, u32 d0,
+                                           u32 nlim, const key_t *dk, const u32 *dv, key_t *ak, u32 *av, u32 *err,
+                                           int tid) {
+  constexpr int U = 8;
+  for (u32 qb = cs; qb < rend; qb += U * 32 * NW) {
+    key_t kk[U];
+    u32 vv[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {  // every load first
+      const u32 q = qb + (u32)(u * 32 * NW + tid);
+      if (q < rend) {
+        const u32 c2 = skew_col_of(seg_pre, nc, q);
+        const u32 p2 = seg_start[c2] + (q - seg_pre[c2]);
+        kk[u] = dk[p2];
+        vv[u] = dv[p2];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const u32 q = qb + (u32)(u * 32 * NW + tid);
+      if (q < rend) {
+        const u32 dest = d0 + (q - cs);
+        if (dest < nlim) {
+          ak[dest] = kk[u];
+          av[dest] = vv[u];
+        } else {
+          atomicOr(err, ERRB_SIZES);
+        }
+      }
+    }
+  }
+}
+
 template <int DT, int CAP>
 struct SkewTagSmem {
   typedef typename KT<DT>::elem_t E;
@@ -1199,7 +1270,8 @@ struct SkewTagSmem {
   u32 cnt[kSkewBkts * (NW + 1)];  // (tag, warp), tag-major, padded rows
   u32 base[kSkewBkts], running[kSkewBkts], ob[kSkewBkts + 1], adj[kSkewBkts];
   u32 seg_start[kSkewCols], seg_pre[kSkewCols + 1];
-  u32 s_u, s_ri, s_S;
+  uint8_t seg_t0[kSkewCols], seg_t1[kSkewCols];  // a big tile's column segments: first and last tag (0xff: empty)
+  u32 s_u, s_ri, s_S, s_big;
 };
 
 template <int DT, int CAP>
@@ -1230,6 +1302,8 @@ __global__ void __launch_bounds__(32 * SQ_SKEW_WARPS, 32 / SQ_SKEW_WARPS) k_skew
     const u32 j0 = Jb * kSkewBkts, nk = min((u32)kSkewBkts, nd.k - j0);
     const u32 i0 = Is * kSkewCols, nc = min((u32)kSkewCols, nd.cols - i0);
     const u32 *P = meta + ML.P;
+    const Inst I = c.inst[nd.inst];
+    const uint8_t *tg = I.tags + nd.off;
     if (warp == 0) {  // the tile's column segments and their prefix sums
       u32 len_seg = 0, st = 0;
       if ((u32)lane < nc) {
@@ -1248,9 +1322,20 @@ __global__ void __launch_bounds__(32 * SQ_SKEW_WARPS, 32 / SQ_SKEW_WARPS) k_skew
       const u32 ex = warp_excl_scan(len_seg, total);
       sm.seg_start[lane] = st;
       sm.seg_pre[lane] = ex;
+      // a big tile (sorted or reversed input: the tile on the diagonal gets
+      // whole columns) notes its segments' first and last tags for the runs
+      const bool big = total >= kSkewBig;
+      u32 t0 = 0xffu, t1 = 0xffu;
+      if (big && len_seg) {
+        t0 = tg[st];
+        t1 = tg[st + len_seg - 1];
+      }
+      sm.seg_t0[lane] = (uint8_t)t0;
+      sm.seg_t1[lane] = (uint8_t)t1;
       if (lane == 0) {
         sm.seg_pre[32] = total;
         sm.s_S = total;
+        sm.s_big = big;
       }
     }
     __syncthreads();
@@ -1262,15 +1347,27 @@ __global__ void __launch_bounds__(32 * SQ_SKEW_WARPS, 32 / SQ_SKEW_WARPS) k_skew
       sm.base[tid] = b[j0 + tid] + G[(u64)(Is * (kSkewCols / kCountCols)) * nd.k + j0 + tid];
       sm.running[tid] = 0;
     }
-    const Inst I = c.inst[nd.inst];
     const key_t *dk = (const key_t *)I.dkeys + nd.off;
     const u32 *dv = I.dvals + nd.off;
-    const uint8_t *tg = I.tags + nd.off;
     key_t *ak = (key_t *)I.keys + nd.off;
     u32 *av = I.vals + nd.off;
     for (int i = tid; i < kSkewBkts * (NW + 1); i += 32 * NW) sm.cnt[i] = 0;
     __syncthreads();
-    for (u32 cs = 0; cs < S; cs += CAP) {
+    for (u32 cs = 0; cs < S;) {
+      if (sm.s_big) {  // a long run of one tag is copied straight to its bucket
+        const u32 rend = skew_tag_run(sm.seg_start, sm.seg_pre, sm.seg_t0, sm.seg_t1, nc, cs, tg, lane);
+        const u32 c0 = skew_col_of(sm.seg_pre, nc, cs);
+        const u32 tS = tg[sm.seg_start[c0] + (cs - sm.seg_pre[c0])];
+        if (tS < nk && rend - cs >= kSkewRunMin) {
+          skew_copy_run<key_t, NW>(sm.seg_start, sm.seg_pre, nc, cs, rend, sm.base[tS] + sm.running[tS], nd.n, dk, dv,
+                                   ak, av, &c.status->error, tid);
+          __syncthreads();  // running[tS] read everywhere
+          if (tid == 0) sm.running[tS] += rend - cs;
+          __syncthreads();
+          cs = rend;
+          continue;
+        }
+      }
       const u32 L = min((u32)CAP, S - cs);
       // warp `warp` takes chunk positions [warp*PW, warp*PW + PW): first every
       // group's column, tag and element (independent loads), then the ranks
@@ -1283,10 +1380,7 @@ __global__ void __launch_bounds__(32 * SQ_SKEW_WARPS, 32 / SQ_SKEW_WARPS) k_skew
         ev[g] = K::top();
         if (ql < L) {
           const u32 q = cs + ql;
-          u32 ci = 0;  // column: the last with seg_pre <= q
-#pragma unroll
-          for (u32 st = 16; st > 0; st >>= 1)
-            if (ci + st < nc && sm.seg_pre[ci + st] <= q) ci += st;
+          const u32 ci = skew_col_of(sm.seg_pre, nc, q);  // the last column with seg_pre <= q
           const u32 p = sm.seg_start[ci] + (q - sm.seg_pre[ci]);
           rt[g] = tg[p];
           ev[g] = K::make(dk[p], dv[p]);
@@ -1364,6 +1458,7 @@ __global__ void __launch_bounds__(32 * SQ_SKEW_WARPS, 32 / SQ_SKEW_WARPS) k_skew
       }
       for (int i = tid; i < kSkewBkts * (NW + 1); i += 32 * NW) sm.cnt[i] = 0;
       __syncthreads();
+      cs += L;
     }
   }
 }
