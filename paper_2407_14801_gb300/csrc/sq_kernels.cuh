@@ -77,10 +77,12 @@ __device__ __forceinline__ int upper_bound_e(const typename K::elem_t *piv, int 
 // holds, given that it is at least lo: the lanes first probe 32 pivots
 // kSpan apart, then the kSpan pivots of the interval found; larger jumps
 // fall back to a binary search.  Replaces a serial search of log2(np) steps.
-template <class K>
+// (kSpan: about the buckets a warp's group of elements spans on uniform
+// input, at most 32.)
+template <class K, int kSpan = 4>
 __device__ __forceinline__ int warp_bucket_from(const typename K::elem_t *piv, int lo, int np,
                                                 const typename K::elem_t &e) {
-  constexpr int kSpan = 4;
+  static_assert(kSpan >= 2 && kSpan <= 32, "probe spacing");
   const int lane = threadIdx.x & 31;
   int idx = lo + (lane + 1) * kSpan - 1;  // probes lo+3, lo+7, ...
   bool le = idx < np && !K::lt(e, piv[idx]);
@@ -748,14 +750,16 @@ __global__ void __launch_bounds__(WARP ? 256 : T) k_pivots(const Ctx *__restrict
 // ----------------------------------------------------------------- count ---
 // One pass over the sorted columns of a block of kCountCols columns
 // (Section 2.2: each sorted column is scanned against the sorted pivots).
-// Every warp streams a contiguous part of the block, one element per lane
-// (coalesced, kCountU groups of loads in flight).  Within a column the
-// buckets of 32 consecutive elements lie between the previous group's last
-// bucket and the bucket of the group's last element, so each lane searches
-// only that range.  Produces the block's per-bucket totals T[I][j] and, per
-// column, the start P[Jb][i] of every kSkewBkts-bucket segment.
+// Every warp streams a contiguous part of the block in groups of 32*kCountR
+// elements, kCountR consecutive ones a lane.  Within a column the group's
+// buckets lie between the previous group's last bucket and the bucket of the
+// group's last element (found by a warp-wide probe); a lane searches that
+// range for its first element and gallops from there for the others.
+// Produces the block's per-bucket totals T[I][j], per column the start
+// P[Jb][i] of every kSkewBkts-bucket segment, and every element's tag (its
+// bucket within its segment) for the SkewTranspose.
 
-constexpr int kCountU = 4;
+constexpr int kCountR = 4;  // count: consecutive elements a lane
 constexpr u32 kPiece = 256;  // skew: elements per warp work piece
 
 template <int DT>
@@ -801,77 +805,122 @@ __global__ void __launch_bounds__(1024) k_count(const Ctx *__restrict__ cp, u32 
     const u32 q0 = (u32)min((u64)i0 * rows, (u64)n);
     const u32 q1 = (u32)min((u64)i1 * rows, (u64)n);
     const u32 S = q1 - q0;
-    const u32 per_warp = (((S + NW - 1) / NW) + 31) & ~31u;
+    constexpr int CR = kCountR;  // consecutive elements a lane, kCountR * 32 a warp group
+    const u32 per_warp = (((S + NW - 1) / NW) + 32 * CR - 1) / (32 * CR) * (32 * CR);
     const u32 ws = q0 + min(S, warp * per_warp);
     const u32 we = q0 + min(S, warp * per_warp + per_warp);
-    // lane position (column i, offset pos) of element ws + lane, advanced 32 per group
-    u32 p_l = ws + lane;
+    // column ci and offset pos of this lane's first element, advanced 32*CR per group
+    const u32 p_l = ws + (u32)(CR * lane);
     u32 ci = p_l / rows, pos = p_l - ci * rows;
     int carry_b = -1;
     u32 carry_i = kNone;
-    for (u32 gs = ws; gs < we; gs += 32 * kCountU) {
-      E ev[kCountU];
+    for (u32 gs = ws; gs < we; gs += 32 * CR) {
+      const u32 pl = gs + (u32)(CR * lane);  // this lane's elements: [pl, pl + CR) within [gs, we)
+      E ev[CR];
 #pragma unroll
-      for (int g = 0; g < kCountU; g++) {
-        const u32 p = gs + g * 32 + lane;
-        ev[g] = p < we ? K::make(dk[p], dv[p]) : K::top();
-      }
+      for (int r = 0; r < CR; r++) ev[r] = pl + r < we ? K::make(dk[pl + r], dv[pl + r]) : K::top();
+      const u32 glast = min(we, gs + 32 * CR) - 1;  // the group's last element
+      const int llast = (int)((glast - gs) / CR), rlast = (int)((glast - gs) % CR);
+      // the column of every element of the lane (a lane crosses at most a few column ends)
+      u32 cr[CR], pr[CR];
+      {
+        u32 c2 = ci, p2 = pos;
 #pragma unroll
-      for (int g = 0; g < kCountU; g++) {
-        const u32 gb = gs + g * 32;
-        if (gb >= we) break;
-        const u32 p = gb + lane;
-        const bool valid = p < we;
-        const u32 vmask = __ballot_sync(0xffffffffu, valid);
-        const int lastv = 31 - __clz(vmask);
-        const u32 len = (u64)ci * rows < n ? min(rows, n - ci * rows) : 0;
-        const u32 i_first = __shfl_sync(0xffffffffu, ci, 0);
-        const u32 i_last = __shfl_sync(0xffffffffu, ci, lastv);
-        const E e = ev[g];
-        int b;
-        if (i_first == i_last) {  // one column: buckets are monotone across the group
-          const u32 pos0 = __shfl_sync(0xffffffffu, pos, 0);
-          const int lo = (i_first == carry_i) ? carry_b : (pos0 == 0 ? 0 : 0);
-          const E elast = shfl_e(e, lastv);
-          const int hi = warp_bucket_from<K>(piv, lo, np, elast);
-          b = upper_bound_e<K>(piv, lo, hi, e);
-        } else {
-          b = upper_bound_e<K>(piv, 0, np, e);
-        }
-        if (tg && valid) tg[p] = (uint8_t)(b & (kSkewBkts - 1));  // for the SkewTranspose
-        // bucket totals: one atomic per run of equal buckets
-        const int prevb = __shfl_up_sync(0xffffffffu, b, 1);
-        const bool start = valid && (lane == 0 || prevb != b);
-        const u32 smask = __ballot_sync(0xffffffffu, start);
-        if (start) {
-          const u32 higher = smask & ~((2u << lane) - 1u);
-          const u32 nxt = higher ? (u32)(__ffs(higher) - 1) : (u32)__popc(vmask);
-          atomicAdd(&hist[b], nxt - lane);
-        }
-        // segment starts P[Jb][i]: the first position whose bucket reaches Jb*kSkewBkts
-        if (valid) {
-          int bp;
-          if (pos == 0) {
-            bp = -1;
-          } else if (lane > 0) {
-            bp = prevb;
-          } else if (carry_i == ci) {
-            bp = carry_b;
-          } else {  // first element of this warp's range, mid-column
-            const E pe = K::make(dk[p - 1], dv[p - 1]);
-            bp = upper_bound_e<K>(piv, 0, np, pe);
+        for (int r = 0; r < CR; r++) {
+          while (p2 >= rows) {
+            p2 -= rows;
+            ++c2;
           }
-          for (int Jb = (bp + kSkewBkts) / kSkewBkts; Jb <= b / kSkewBkts; ++Jb) P[(u64)Jb * cols + ci] = pos;
-          if (pos + 1 == len)
-            for (u32 Jb = b / kSkewBkts + 1; Jb < nkb; ++Jb) P[(u64)Jb * cols + ci] = len;
+          cr[r] = c2;
+          pr[r] = p2;
+          ++p2;
         }
-        carry_b = __shfl_sync(0xffffffffu, b, lastv);
-        carry_i = __shfl_sync(0xffffffffu, ci, lastv);
-        pos += 32;
-        while (pos >= rows) {
-          pos -= rows;
-          ++ci;
+      }
+      u32 my_last_c = cr[0];
+      E my_last_e = ev[0];
+#pragma unroll
+      for (int r = 1; r < CR; r++)
+        if (r == rlast) {
+          my_last_c = cr[r];
+          my_last_e = ev[r];
         }
+      const u32 i_first = __shfl_sync(0xffffffffu, ci, 0);
+      const u32 i_last = __shfl_sync(0xffffffffu, my_last_c, llast);
+      int bk[CR];
+      if (i_first == i_last) {  // one column: buckets ascend through the group
+        const int lo = i_first == carry_i ? carry_b : 0;
+        const E elast = shfl_e(my_last_e, llast);
+        const int hi = warp_bucket_from<K, 4 * CR>(piv, lo, np, elast);
+        bk[0] = upper_bound_e<K>(piv, lo, hi, ev[0]);
+#pragma unroll
+        for (int r = 1; r < CR; r++) {  // gallop from the previous element's bucket
+          int lo2 = bk[r - 1], st = 1, b = hi;
+          for (;;) {
+            const int idx = lo2 + st - 1;
+            if (idx >= hi) {
+              b = upper_bound_e<K>(piv, lo2, hi, ev[r]);
+              break;
+            }
+            if (K::lt(ev[r], piv[idx])) {
+              b = upper_bound_e<K>(piv, lo2, idx, ev[r]);
+              break;
+            }
+            lo2 = idx + 1;
+            st <<= 1;
+          }
+          bk[r] = b;
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < CR; r++) bk[r] = upper_bound_e<K>(piv, 0, np, ev[r]);
+      }
+      // the bucket before each element in its column (-1 at a column start)
+      const int prev_lane_b = __shfl_up_sync(0xffffffffu, bk[CR - 1], 1);
+      int lastb = bk[0];
+#pragma unroll
+      for (int r = 1; r < CR; r++)
+        if (r == rlast) lastb = bk[r];
+      int runb = -1;
+      u32 runc = 0;
+#pragma unroll
+      for (int r = 0; r < CR; r++) {
+        const u32 p = pl + (u32)r;
+        if (p >= we) break;
+        const int b = bk[r];
+        if (tg) tg[p] = (uint8_t)(b & (kSkewBkts - 1));  // for the SkewTranspose
+        if (b != runb) {  // bucket totals: one atomic per run of equal buckets in the lane
+          if (runc) atomicAdd(&hist[runb], runc);
+          runb = b;
+          runc = 0;
+        }
+        ++runc;
+        // segment starts P[Jb][i]: the first position whose bucket reaches Jb*kSkewBkts
+        const u32 c2 = cr[r], q = pr[r];
+        const u32 len = (u64)c2 * rows < n ? min(rows, n - c2 * rows) : 0;
+        int bp;
+        if (q == 0) {
+          bp = -1;
+        } else if (r > 0) {
+          bp = bk[r - 1];
+        } else if (lane > 0) {
+          bp = prev_lane_b;
+        } else if (carry_i == c2) {
+          bp = carry_b;
+        } else {  // first element of this warp's range, mid-column
+          const E pe = K::make(dk[p - 1], dv[p - 1]);
+          bp = upper_bound_e<K>(piv, 0, np, pe);
+        }
+        for (int Jb = (bp + kSkewBkts) / kSkewBkts; Jb <= b / kSkewBkts; ++Jb) P[(u64)Jb * cols + c2] = q;
+        if (q + 1 == len)
+          for (u32 Jb = b / kSkewBkts + 1; Jb < nkb; ++Jb) P[(u64)Jb * cols + c2] = len;
+      }
+      if (runc) atomicAdd(&hist[runb], runc);
+      carry_b = __shfl_sync(0xffffffffu, lastb, llast);
+      carry_i = i_last;
+      pos += 32 * CR;
+      while (pos >= rows) {
+        pos -= rows;
+        ++ci;
       }
     }
     __syncthreads();
