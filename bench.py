@@ -414,6 +414,10 @@ def bench_e2e(sq, n, steps, dev, inputs):
     iota = torch.arange(n, dtype=torch.int32)
     names = list(inputs)
     src = {d: inputs[d].cpu() for d in names[:steps]}
+    for i in range(2):  # untimed: the first calls grow the device memory pool
+        hk.copy_(src[names[i % len(src)]])
+        hv.copy_(iota)
+        sq.sort(hk, hv, seed=90 + i, dtype="u32")
     tot = 0.0
     for i in range(steps):
         d = names[i % len(names)]
@@ -424,7 +428,8 @@ def bench_e2e(sq, n, steps, dev, inputs):
         sq.sort(hk, hv, seed=100 + i, dtype="u32")  # H2D, sort, D2H inside the call
         tot += time.perf_counter() - t0
     return {"value": round(steps * n / tot / 1e9, 3), "unit": UNIT, "h2d_bytes_per_step": 8 * n,
-            "d2h_bytes_per_step": 8 * n, "steps": steps, "buffers": "pinned host"}
+            "d2h_bytes_per_step": 8 * n, "steps": steps, "warmup": 2,
+            "buffers": "pinned host, read by the first pass and written by the last through the device mapping"}
 
 
 def cpu_baseline(sample_log2: int = 23, budget_s: float = 25.0):

@@ -10,8 +10,11 @@
  *
  * Conventions for every call below:
  *  - Pointers are plain addresses.  Key and payload buffers may be device
- *    memory (the fast path) or, for sq_sort / sq_sort_ex only, host memory,
- *    which is staged through device memory inside the call.
+ *    memory (the fast path) or, for sq_sort / sq_sort_ex only, host memory.
+ *    Page-locked (pinned, mapped) host buffers are read by the first pass
+ *    and written by the last pass directly through the device mapping, with
+ *    device memory only for the rounds between; other host memory is staged
+ *    through device memory inside the call.
  *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Device
  *    work is ordered on it; calls return after the work is finished (the
  *    engine reads per-round work counts back to the host).

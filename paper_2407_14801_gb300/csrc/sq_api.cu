@@ -90,6 +90,26 @@ bool is_host_ptr(const void *p) {
   return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
 }
 
+// The device address of a page-locked host buffer (mapped into the device's
+// address space), else NULL.
+void *mapped_host(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// Where the first pass reads and the last pass writes, when not the sorted
+// buffers themselves (NULL members: the buffers).
+struct SrcFin {
+  const void *skeys;
+  const uint32_t *svals;
+  void *fkeys;
+  uint32_t *fvals;
+};
+
 __global__ void k_iota(uint32_t *v, uint64_t n) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
     v[i] = (uint32_t)i;
@@ -105,7 +125,7 @@ struct DevBuf {
 
 // Sorts one instance whose buffers are device memory.
 sq_status sort_device(void *keys, uint32_t *vals, uint64_t n, sq_dtype dtype, uint64_t seed, cudaStream_t st,
-                      const sq_sort_opts *opts) {
+                      const sq_sort_opts *opts, const SrcFin *io = nullptr) {
   const uint32_t cutoff = (opts && opts->cutoff) ? opts->cutoff : cutoff_for(dtype, n);
   const size_t w = key_bytes(dtype);
   keep_pool_cached();
@@ -129,6 +149,12 @@ sq_status sort_device(void *keys, uint32_t *vals, uint64_t n, sq_dtype dtype, ui
   is.dkeys = scratch.p;
   is.dvals = (uint32_t *)((char *)scratch.p + dk_bytes);
   is.tags = (uint8_t *)scratch.p + dk_bytes + dv_bytes;
+  if (io) {
+    is.skeys = io->skeys;
+    is.svals = io->svals;
+    is.fkeys = io->fkeys;
+    is.fvals = io->fvals;
+  }
   is.n = n;
   is.seed = seed;
   sq::RunSpec spec;
@@ -231,12 +257,30 @@ sq_status sq_sort_ex(void *keys, uint32_t *vals, uint64_t n, sq_dtype dtype, uin
   const size_t w = key_bytes(dtype);
   const bool hk = is_host_ptr(keys), hv = vals && is_host_ptr(vals);
   if (!hk && !hv) return sort_device(keys, vals, n, dtype, seed, st, opts);
-  // host buffers: stage through device memory
+  cudaError_t e;
+  void *mk = hk ? mapped_host(keys) : nullptr;
+  uint32_t *mv = hv ? (uint32_t *)mapped_host(vals) : nullptr;
+  if (hk && mk && (!vals || mv)) {
+    // page-locked host buffers: the first pass (the root's column sorts, or
+    // a single leaf) reads them and the last pass (the final leaves) writes
+    // them, through the mapping; device memory holds only the rounds between
+    DevBuf ak, av;
+    ak.st = av.st = st;
+    if ((e = cudaMallocAsync(&ak.p, n * w, st)) != cudaSuccess)
+      return fail(SQ_ERR_NOMEM, "device keys: %s", cudaGetErrorString(e));
+    if (vals && (e = cudaMallocAsync(&av.p, n * 4, st)) != cudaSuccess)
+      return fail(SQ_ERR_NOMEM, "device vals: %s", cudaGetErrorString(e));
+    const SrcFin io{mk, mv, mk, mv};
+    const sq_status s = sort_device(ak.p, vals ? (uint32_t *)av.p : nullptr, n, dtype, seed, st, opts, &io);
+    if (s != SQ_OK) return s;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(SQ_ERR_CUDA, "%s", cudaGetErrorString(e));
+    return SQ_OK;
+  }
+  // other host buffers: staged through device memory
   DevBuf dk, dv;
   dk.st = dv.st = st;
   void *k = keys;
   uint32_t *v = vals;
-  cudaError_t e;
   if (hk) {
     if ((e = cudaMallocAsync(&dk.p, n * w, st)) != cudaSuccess)
       return fail(SQ_ERR_NOMEM, "staging keys: %s", cudaGetErrorString(e));

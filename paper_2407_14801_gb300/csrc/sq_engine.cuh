@@ -678,6 +678,10 @@ struct Engine {
       hinst[i].vals = is.vals;
       hinst[i].dkeys = is.dkeys;
       hinst[i].dvals = is.dvals;
+      hinst[i].skeys = is.skeys ? is.skeys : is.keys;
+      hinst[i].svals = is.svals ? is.svals : is.vals;
+      hinst[i].fkeys = is.fkeys ? is.fkeys : is.keys;
+      hinst[i].fvals = is.fvals ? is.fvals : is.vals;
       hinst[i].tags = is.tags;
       hinst[i].n = is.n;
       hinst[i].cutoff = cutoff_of(i);
@@ -695,7 +699,7 @@ struct Engine {
         L.n = (u32)is.n;
         L.inst = i;
         L.parent = kNone;
-        L.flags = KIND_ROOT;  // out = A
+        L.flags = KIND_ROOT | LEAF_SRC;  // from the source into A (or the final buffer)
         hleaves[cl].push_back(L);
         hc[0].leaf_elems[cl] += is.n;
       } else {
@@ -710,6 +714,7 @@ struct Engine {
         nd.parent = kNone;
         nd.kind = KIND_ROOT;
         nd.out = 0;
+        nd.src = 1;
         const u32 id = (u32)hnodes.size();
         if (m <= hinst[i].cutoff && m >= kHostExpandCols) {
           // a large root whose columns are leaves: spawn them here rather than
@@ -723,7 +728,7 @@ struct Engine {
             L.n = (u32)std::min<u64>(m, is.n - st0);
             L.inst = i;
             L.parent = id;
-            L.flags = KIND_COL | (1u << 8);  // columns are sorted from A into D
+            L.flags = KIND_COL | (1u << 8) | LEAF_SRC;  // the root's columns: from the source into D
             const int cl = class_of(L.n, NCLASS);
             hleaves[cl].push_back(L);
             hc[0].leaf_elems[cl] += L.n;
@@ -1069,6 +1074,10 @@ struct Engine {
       hi.vals = is.vals;
       hi.dkeys = is.dkeys;
       hi.dvals = is.dvals;
+      hi.skeys = is.skeys ? is.skeys : is.keys;
+      hi.svals = is.svals ? is.svals : is.vals;
+      hi.fkeys = is.fkeys ? is.fkeys : is.keys;
+      hi.fvals = is.fvals ? is.fvals : is.vals;
       hi.tags = is.tags;
       hi.n = is.n;
       hi.cutoff = cut;
@@ -1087,7 +1096,7 @@ struct Engine {
         L.n = (u32)is.n;
         L.inst = slot;
         L.parent = kNone;
-        L.flags = KIND_ROOT;
+        L.flags = KIND_ROOT | LEAF_SRC;
         put_leaf(L);
       } else {
         if (int rc = grow_nodes((u64)nodes_used + 1 + P.fresh_cap, err, errlen)) return rc;
@@ -1101,6 +1110,7 @@ struct Engine {
         nd.parent = kNone;
         nd.kind = KIND_ROOT;
         nd.out = 0;
+        nd.src = 1;
         has_node = true;
         const u32 id = nodes_used;
         if (m <= cut && m >= kHostExpandCols) {  // its columns are leaves: spawn them here
@@ -1112,7 +1122,7 @@ struct Engine {
             L.n = (u32)std::min<u64>(m, is.n - L.off);
             L.inst = slot;
             L.parent = id;
-            L.flags = KIND_COL | (1u << 8);
+            L.flags = KIND_COL | (1u << 8) | LEAF_SRC;
             put_leaf(L);
           }
         } else {

@@ -37,6 +37,12 @@ struct InstSpec {
   void *dkeys;     // D keys scratch (device), same length
   uint32_t *dvals; // D vals scratch (device)
   uint8_t *tags;   // n bytes of scratch (device) for bucket tags; NULL: the SkewTranspose classifies
+  // Optional (NULL: keys / vals): where the first pass reads the input and
+  // where the last pass writes the result, e.g. mapped pinned host buffers.
+  const void *skeys;
+  const uint32_t *svals;
+  void *fkeys;
+  uint32_t *fvals;
   uint64_t n;
   uint64_t seed;
   uint32_t cutoff;  // 0: RunSpec::cutoff

@@ -361,11 +361,13 @@ __global__ void __launch_bounds__(WARP ? 256 : T, kLeafMinBlocks<DT, T, WARP>())
     const Inst I = c.inst[L.inst];
     E *s = smem + g * S::SMEM;
     E x[R];
-    const u32 out = L.flags >> 8;
-    const key_t *ik = (const key_t *)I.keys + L.off;
-    const u32 *iv = I.vals + L.off;
-    key_t *ok = (key_t *)(out ? I.dkeys : I.keys) + L.off;
-    u32 *ov = (out ? I.dvals : I.vals) + L.off;
+    const u32 out = (L.flags >> 8) & 0xffu;
+    const bool from_src = (L.flags & LEAF_SRC) != 0;
+    const key_t *ik = (const key_t *)(from_src ? I.skeys : I.keys) + L.off;
+    const u32 *iv = (from_src ? I.svals : I.vals) + L.off;
+    key_t *ok = (key_t *)(out ? I.dkeys : I.fkeys) + L.off;
+    u32 *ov = (out ? I.dvals : I.fvals) + L.off;
+    const bool moves = (const void *)ik != (const void *)ok || iv != ov;  // else sorted in place
     u32 nn = 0;
     if constexpr (K::lossy) {
       if (tid == 0) nl[0] = 0;
@@ -376,7 +378,7 @@ __global__ void __launch_bounds__(WARP ? 256 : T, kLeafMinBlocks<DT, T, WARP>())
       nn = nl[0];
       S::sync();  // read before the list is reset for the group's next leaf
       if (nn > kNanCap) {  // too many to restore: the fix list's exact (key, val) sort takes the leaf
-        if (out)
+        if (moves)
           for (u32 p = tid; p < L.n; p += T) {
             ok[p] = ik[p];
             ov[p] = iv[p];
@@ -394,13 +396,13 @@ __global__ void __launch_bounds__(WARP ? 256 : T, kLeafMinBlocks<DT, T, WARP>())
       S::sync();  // (the moved leaf is written before its NaNs get their bits back)
     }
     if (pre == 0) S::sort(x, s, tid);
-    if (pre < 4 && (pre != 1 || out)) {  // (a sorted leaf in place is left as it is)
+    if (pre < 4 && (pre != 1 || moves)) {  // (a sorted leaf in place is left as it is)
       const int n = (int)L.n, r = pre == 3 ? (int)rot : 0;
       const bool rev = pre == 2;
       S::store_mapped(x, s, tid, ok, ov, L.n, [&](int i) { return rev ? n - 1 - i : (i >= r ? i - r : i + n - r); });
     }
     if constexpr (K::lossy) {
-      if (nn && (pre != 1 || out)) {  // (a sorted leaf left in place kept its bits)
+      if (nn && (pre != 1 || moves)) {  // (a sorted leaf left in place kept its bits)
         for (u32 i = tid; i < nn; i += T) ok[L.n - nn + nan_rank(nl, nn, nl[1 + i], i)] = (key_t)nl[1 + kNanCap + i];
         S::sync();
       }
@@ -451,10 +453,12 @@ __global__ void __launch_bounds__(T, (T <= 512 && sizeof(typename KT<DT>::elem_t
     const u64 off = L.off + (u64)rank * CS::NC;
     const u32 nr = L.n > (u32)rank * CS::NC ? min((u32)CS::NC, L.n - (u32)rank * CS::NC) : 0u;
     const u32 out = (L.flags >> 8) & 0xffu;
-    const key_t *ik = (const key_t *)I.keys + L.off;
-    const u32 *iv = I.vals + L.off;
-    key_t *ok = (key_t *)(out ? I.dkeys : I.keys) + L.off;
-    u32 *ov = (out ? I.dvals : I.vals) + L.off;
+    const bool from_src = (L.flags & LEAF_SRC) != 0;
+    const key_t *ik = (const key_t *)(from_src ? I.skeys : I.keys) + L.off;
+    const u32 *iv = (from_src ? I.svals : I.vals) + L.off;
+    key_t *ok = (key_t *)(out ? I.dkeys : I.fkeys) + L.off;
+    u32 *ov = (out ? I.dvals : I.fvals) + L.off;
+    const bool moves = (const void *)ik != (const void *)ok || iv != ov;  // else sorted in place
     const u32 q0 = (u32)rank * CS::NC;  // this CTA's part of the leaf: [q0, q0 + nr)
     E x[R];
     u32 nn = 0, total = 0;
@@ -474,7 +478,7 @@ __global__ void __launch_bounds__(T, (T <= 512 && sizeof(typename KT<DT>::elem_t
       nn = nl[0];
       cl.sync();  // the counts are read before any list changes
       if (most > kNanCap) {  // too many to restore: the fix list's exact (key, val) sort takes the leaf
-        if (out)
+        if (moves)
           for (u32 p = tid; p < nr; p += T) {
             ok[q0 + p] = ik[q0 + p];
             ov[q0 + p] = iv[q0 + p];
@@ -493,11 +497,11 @@ __global__ void __launch_bounds__(T, (T <= 512 && sizeof(typename KT<DT>::elem_t
     }
     if (pre <= 1) {
       if (pre == 0) CS::sort(x, s, tid, (int)L.n);
-      if (pre == 0 || out) S::store(x, s, tid, ok + q0, ov + q0, nr);  // a sorted leaf in place stays
+      if (pre == 0 || moves) S::store(x, s, tid, ok + q0, ov + q0, nr);  // a sorted leaf in place stays
     }
     cl.sync();  // (also: no part changes before every CTA has read what it moves)
     if constexpr (K::lossy) {
-      if (total && (pre != 1 || out)) {  // the leaf's NaNs end it, in val order (then by part, entry)
+      if (total && (pre != 1 || moves)) {  // the leaf's NaNs end it, in val order (then by part, entry)
         for (u32 i = tid; i < nn; i += T) {
           const u32 v = nl[1 + i];
           u32 r = 0;
@@ -547,8 +551,8 @@ __global__ void __launch_bounds__(T, 1) k_fixup(const Ctx *__restrict__ cp) {
     const Leaf L = c.fix[item];
     const Inst I = c.inst[L.inst];
     const u32 out = (L.flags >> 8) & 0xffu;
-    key_t *kk = (key_t *)(out ? I.dkeys : I.keys) + L.off;
-    u32 *vv = (out ? I.dvals : I.vals) + L.off;
+    key_t *kk = (key_t *)(out ? I.dkeys : I.fkeys) + L.off;
+    u32 *vv = (out ? I.dvals : I.fvals) + L.off;
     const u64 off = (u64)rank * CS::NC;
     const u32 nr = L.n > (u32)off ? min((u32)CS::NC, L.n - (u32)off) : 0u;
     E x[R];
@@ -1519,7 +1523,7 @@ __global__ void __launch_bounds__(32 * SQ_SKEW_WARPS, 32 / SQ_SKEW_WARPS) k_skew
 struct Child {
   u64 off;
   u64 hash;
-  u32 n, inst, parent, kind, index, depth, out;
+  u32 n, inst, parent, kind, index, depth, out, src;
 };
 
 static __device__ void spawn_batch(const Ctx &c, bool has, const Child &ch, u32 *fresh_list, u32 *fresh_count,
@@ -1558,7 +1562,7 @@ static __device__ void spawn_batch(const Ctx &c, bool has, const Child &ch, u32 
         L.n = ch.n;
         L.inst = ch.inst;
         L.parent = ch.parent;
-        L.flags = ch.kind | (ch.out << 8);
+        L.flags = ch.kind | (ch.out << 8) | (ch.src ? LEAF_SRC : 0u);
         c.leaves_nxt[cls][idx] = L;
       } else {
         atomicOr(&c.status->error, ERRB_LIST);
@@ -1584,7 +1588,7 @@ static __device__ void spawn_batch(const Ctx &c, bool has, const Child &ch, u32 
         nn.attempts = 0;
         nn.unit_base = nn.tile_base = nn.srow_base = 0;
         nn.ncb = nn.nkb = nn.ncs = 0;
-        nn.pad = 0;
+        nn.src = ch.src;
         c.nodes[id] = nn;
         fresh_list[fi] = id;
       } else {
@@ -1633,6 +1637,7 @@ __global__ void __launch_bounds__(256) k_expand_buckets(const Ctx *__restrict__ 
       ch.index = j;
       ch.depth = nd.depth + 1;
       ch.out = nd.out;
+      ch.src = 0;  // a bucket reads what its parent's SkewTranspose wrote
     }
     spawn_batch(c, has, ch, c.fresh_cur, &c.cnt_cur->fresh, LeafCfg<DT>::nclass);
   }
@@ -1668,6 +1673,7 @@ __global__ void __launch_bounds__(256) k_expand_cols(const Ctx *__restrict__ cp)
         ch.index = i;
         ch.depth = nd.depth + 1;
         ch.out = 1;  // columns are sorted from A into D
+        ch.src = nd.src;  // (reading where the node's own input lies)
       }
       spawn_batch(c, has, ch, c.fresh_nxt, &c.cnt_nxt->fresh, LeafCfg<DT>::nclass);
     }

@@ -204,6 +204,10 @@ struct Inst {
   u32 *vals;   // A vals
   void *dkeys; // D keys (scratch)
   u32 *dvals;  // D vals (scratch)
+  const void *skeys;  // where the input is read (the root's columns, or the root leaf): A, or a mapped
+  const u32 *svals;   //   host buffer that the first pass reads directly
+  void *fkeys;        // where final leaves write: A, or a mapped host buffer that the last pass
+  u32 *fvals;         //   writes directly
   uint8_t *tags;  // per element of D: its bucket within its 64-bucket block (written by the count)
   u64 n;
   u32 cutoff;  // leaf iff a node's n <= cutoff (per instance)
@@ -224,15 +228,16 @@ struct Node {
   u32 attempts;
   u32 unit_base, tile_base, srow_base;  // this round's work numbering
   u32 ncb, nkb, ncs;                    // count blocks, bucket blocks, skew column blocks
-  u32 pad;
+  u32 src;  // 1: the node's input is the instance's source (the root, and column children of such nodes)
 };
 
 // A leaf: sorted in one group of threads (n <= cutoff).
 struct Leaf {
   u64 off;
-  u32 n, inst, parent, flags;  // flags: kind | out << 8 | LEAF_IN_OUT
+  u32 n, inst, parent, flags;  // flags: kind | out << 8 | LEAF_IN_OUT | LEAF_SRC
 };
 constexpr u32 LEAF_IN_OUT = 1u << 16;  // input already sits in the output buffer
+constexpr u32 LEAF_SRC = 1u << 17;     // input is read from the instance's source (Inst::skeys)
 
 // Per-parity list counters (zeroed before the round that fills them).
 struct Counters {

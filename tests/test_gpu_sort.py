@@ -272,3 +272,42 @@ def test_presorted_leaves_wide_keys(sq, n):
         check_against_oracle(sq, keys.copy(), vals.copy(), "f32", seed=3, cutoff=65536)
         if n > 8192:
             check_against_oracle(sq, keys.copy(), vals.copy(), "f32", seed=3, cutoff=2048)
+
+
+@pytest.mark.parametrize("dtype", ["u32", "u64", "f32"])
+def test_pinned_host_buffers_are_read_and_written_in_place(sq, dtype):
+    """sq_sort on page-locked host buffers: the first pass reads them and the
+    last pass writes them through the device mapping (no staging copies).
+    A single leaf, one level, and deep recursions whose column nodes read the
+    host input at every depth; sorted input (whose buckets are copied, not
+    skipped); float32 leaves with more NaNs than a leaf restores (the exact
+    fix-up sort then runs in the host buffer); no payload."""
+    gen = {"u32": lambda n, s: W.uniform_u32(n, s), "u64": lambda n, s: W.zipf_u64(n, s),
+           "f32": lambda n, s: W.normal_f32(n, s, p_inf=0.01, p_negzero=0.01, p_nan=0.02)}[dtype]
+    view = {"u32": torch.int32, "u64": torch.int64, "f32": torch.float32}[dtype]
+    cases = [(5000, 65536), (300000, 65536), (70000, 16), (5000, 3), (1 << 20, 4096)]
+    if dtype == "u32":
+        cases.append(("sorted", 65536))
+    for n, cutoff in cases:
+        if n == "sorted":
+            keys = np.sort(W.uniform_u32(1 << 20, 5))
+            n = keys.size
+        else:
+            keys = gen(n, n)
+        vals = np.random.default_rng(n).permutation(n).astype(np.uint32)
+        hk = torch.from_numpy(keys.view(TORCH_VIEW[dtype]) if dtype != "f32" else keys.copy()).pin_memory()
+        hv = torch.from_numpy(vals.view(np.int32)).pin_memory()
+        assert hk.dtype == view and hk.is_pinned() and hv.is_pinned()
+        sq.sort(hk, hv, seed=n, dtype=dtype, cutoff=cutoff)
+        ok, ov, _, _ = oracle.sort(keys, vals, seed=n, cutoff=cutoff, dtype=dtype)
+        got = hk.numpy().view({"u32": np.uint32, "u64": np.uint64, "f32": np.uint32}[dtype])
+        want = ok.view(np.uint32) if dtype == "f32" else ok
+        assert (got == want).all(), (n, cutoff, "keys differ")
+        assert (hv.numpy().view(np.uint32) == ov).all(), (n, cutoff, "payloads differ")
+    # no payload
+    keys = gen(100000, 3)
+    hk = torch.from_numpy(keys.view(TORCH_VIEW[dtype]) if dtype != "f32" else keys.copy()).pin_memory()
+    sq.sort(hk, None, seed=2, dtype=dtype, cutoff=1000)
+    ok, _, _, _ = oracle.sort(keys, None, seed=2, cutoff=1000, dtype=dtype)
+    got = hk.numpy().view({"u32": np.uint32, "u64": np.uint64, "f32": np.uint32}[dtype])
+    assert (got == (ok.view(np.uint32) if dtype == "f32" else ok)).all()
