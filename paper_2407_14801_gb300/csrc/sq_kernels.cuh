@@ -878,20 +878,40 @@ __global__ void __launch_bounds__(1024) k_count(const Ctx *__restrict__ cp, u32 
 #pragma unroll
         for (int r = 0; r < CR; r++) bk[r] = upper_bound_e<K>(piv, 0, np, ev[r]);
       }
-      // the bucket before each element in its column (-1 at a column start)
-      const int prev_lane_b = __shfl_up_sync(0xffffffffu, bk[CR - 1], 1);
+      // the bucket before the lane's first element (in its column; -1 at a column start)
+      int bprev = __shfl_up_sync(0xffffffffu, bk[CR - 1], 1);
+      if (lane == 0) {
+        if (carry_i == cr[0]) {
+          bprev = carry_b;
+        } else if (pr[0] != 0 && pl < we) {  // first element of this warp's range, mid-column
+          const E pe = K::make(dk[pl - 1], dv[pl - 1]);
+          bprev = upper_bound_e<K>(piv, 0, np, pe);
+        }
+      }
       int lastb = bk[0];
 #pragma unroll
       for (int r = 1; r < CR; r++)
         if (r == rlast) lastb = bk[r];
+      const u32 nv = pl < we ? min((u32)CR, we - pl) : 0u;  // the lane's valid elements
+      if (tg) {  // tags for the SkewTranspose: one word when the lane's four are whole and aligned
+        uint8_t *tp = tg + pl;
+        if (CR == 4 && nv == 4 && ((uintptr_t)tp & 3) == 0) {
+          u32 wv = 0;
+#pragma unroll
+          for (int r = 0; r < CR; r++) wv |= (u32)(bk[r] & (kSkewBkts - 1)) << (8 * r);
+          *reinterpret_cast<u32 *>(tp) = wv;
+        } else {
+#pragma unroll
+          for (int r = 0; r < CR; r++)
+            if ((u32)r < nv) tp[r] = (uint8_t)(bk[r] & (kSkewBkts - 1));
+        }
+      }
       int runb = -1;
       u32 runc = 0;
 #pragma unroll
       for (int r = 0; r < CR; r++) {
-        const u32 p = pl + (u32)r;
-        if (p >= we) break;
+        if ((u32)r >= nv) break;
         const int b = bk[r];
-        if (tg) tg[p] = (uint8_t)(b & (kSkewBkts - 1));  // for the SkewTranspose
         if (b != runb) {  // bucket totals: one atomic per run of equal buckets in the lane
           if (runc) atomicAdd(&hist[runb], runc);
           runb = b;
@@ -900,23 +920,12 @@ __global__ void __launch_bounds__(1024) k_count(const Ctx *__restrict__ cp, u32 
         ++runc;
         // segment starts P[Jb][i]: the first position whose bucket reaches Jb*kSkewBkts
         const u32 c2 = cr[r], q = pr[r];
-        const u32 len = (u64)c2 * rows < n ? min(rows, n - c2 * rows) : 0;
-        int bp;
-        if (q == 0) {
-          bp = -1;
-        } else if (r > 0) {
-          bp = bk[r - 1];
-        } else if (lane > 0) {
-          bp = prev_lane_b;
-        } else if (carry_i == c2) {
-          bp = carry_b;
-        } else {  // first element of this warp's range, mid-column
-          const E pe = K::make(dk[p - 1], dv[p - 1]);
-          bp = upper_bound_e<K>(piv, 0, np, pe);
-        }
-        for (int Jb = (bp + kSkewBkts) / kSkewBkts; Jb <= b / kSkewBkts; ++Jb) P[(u64)Jb * cols + c2] = q;
+        const int bp = q == 0 ? -1 : (r > 0 ? bk[r - 1] : bprev);
+        const u32 jb1 = (u32)b / kSkewBkts;
+        for (u32 Jb = (u32)(bp + kSkewBkts) / kSkewBkts; Jb <= jb1; ++Jb) P[(u64)Jb * cols + c2] = q;
+        const u32 len = min(rows, n - c2 * rows);  // (c2 * rows <= q's position < n)
         if (q + 1 == len)
-          for (u32 Jb = b / kSkewBkts + 1; Jb < nkb; ++Jb) P[(u64)Jb * cols + c2] = len;
+          for (u32 Jb = jb1 + 1; Jb < nkb; ++Jb) P[(u64)Jb * cols + c2] = len;
       }
       if (runc) atomicAdd(&hist[runb], runc);
       carry_b = __shfl_sync(0xffffffffu, lastb, llast);
