@@ -379,17 +379,18 @@ def bench_wide(args, sq, dist, rank, world, local):
         hv = torch.empty(n, dtype=torch.int32).pin_memory()
         iota_h = torch.arange(n, dtype=torch.int32)
         tot, reps = 0.0, min(args.steps, 2)
-        for i in range(reps):
+        for i in range(-1, reps):  # (the first round untimed: it grows the device memory pool)
             for d in src:
                 pins[d].copy_(hosts[d])
                 hv.copy_(iota_h)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 sq.sort(pins[d], hv, seed=100 + i, dtype=d)
-                tot += time.perf_counter() - t0
+                if i >= 0:
+                    tot += time.perf_counter() - t0
         e2e = {"value": round(reps * 2 * n / tot / 1e9, 3), "unit": UNIT,
-               "h2d_bytes_per_step": (12 + 8) * n, "d2h_bytes_per_step": (12 + 8) * n, "steps": reps,
-               "buffers": "pinned host"}
+               "h2d_bytes_per_step": (12 + 8) * n, "d2h_bytes_per_step": (12 + 8) * n, "steps": reps, "warmup": 1,
+               "buffers": "pinned host, read by the first pass and written by the last through the device mapping"}
     return {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
@@ -596,13 +597,22 @@ def bench_serve(args, sq, dist, rank, world, local):
 
     import workloads as W
 
+    import torch
+
     nreq = args.serve_requests
     reqs = W.serve_requests(nreq, 11, rate_per_s=1.0)  # arrival times rescaled below
     inputs = [(W.keys_for(dt, n, ks), W.iota(n), dt) for (_, n, dt, ks) in reqs]
     budget = 16 << 30
+    # request buffers in page-locked host memory (as a serving process keeps
+    # them), so that the server's copies run at the host link's rate
+    tdt = {"u32": torch.int32, "u64": torch.int64, "f32": torch.float32}
+    bufs = [(torch.empty(k.size, dtype=tdt[dt]).pin_memory().numpy().view(k.dtype),
+             torch.empty(v.size, dtype=torch.int32).pin_memory().numpy().view(v.dtype), dt) for k, v, dt in inputs]
 
     def run(rate):
-        bufs = [(k.copy(), v.copy(), dt) for k, v, dt in inputs]
+        for (k0, v0, _), (k, v, _) in zip(inputs, bufs):
+            k[...] = k0
+            v[...] = v0
         srv = sq.Server(budget, device=local)
         lat, tickets = [], []
         t0 = time.perf_counter()
@@ -642,6 +652,7 @@ def bench_serve(args, sq, dist, rank, world, local):
             "config": {"workload": f"serve_{nreq}_poisson_requests_2^10..2^24", "requests": nreq,
                        "mean_keys": keys_total / nreq, "budget_bytes": budget,
                        "arrival_rate_rps": round(0.8 * sat_rps, 2), "saturation_rps": round(sat_rps, 2),
+                       "request_buffers": "pinned host",
                        "saturation_keys_per_s": round(keys_total / wall_sat / 1e9, 3)},
             "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                           "mean": float(lat.mean())},

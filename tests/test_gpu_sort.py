@@ -311,3 +311,17 @@ def test_pinned_host_buffers_are_read_and_written_in_place(sq, dtype):
     ok, _, _, _ = oracle.sort(keys, None, seed=2, cutoff=1000, dtype=dtype)
     got = hk.numpy().view({"u32": np.uint32, "u64": np.uint64, "f32": np.uint32}[dtype])
     assert (got == (ok.view(np.uint32) if dtype == "f32" else ok)).all()
+
+
+@pytest.mark.parametrize("dtype", ["u64", "f32"])
+def test_sorted_and_reversed_wide_keys_through_the_skew(sq, dtype):
+    """Sorted and reversed uint64 / float32 input large enough that the
+    SkewTranspose's diagonal tiles copy runs of one tag straight to their
+    bucket (16-byte elements in the copy path), against the oracle."""
+    n = 1 << 21
+    if dtype == "u64":
+        base = np.sort(W.zipf_u64(n, 9))
+    else:
+        base = np.sort(W.normal_f32(n, 9, p_inf=0.001, p_negzero=0.001, p_nan=0.0))
+    for keys in (base, base[::-1].copy()):
+        check_against_oracle(sq, keys.copy(), W.iota(n), dtype, seed=4, cutoff=16384)
