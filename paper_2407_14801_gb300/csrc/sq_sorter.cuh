@@ -180,6 +180,43 @@ struct Sorter {
   template <class Obs>
   __device__ static void load(E (&x)[R], E *s, int tid, const typename K::key_t *keys, const u32 *vals, u32 n,
                               Obs obs) {
+    if constexpr (K::async_load) {
+      // asynchronous copies put the key's and the val's bytes straight into
+      // the element's slot in shared memory, every copy of the thread in
+      // flight at once and no register held for them; then each thread
+      // completes its own slots (K::raw) and observes them
+#pragma unroll
+      for (int k = 0; k < R; k++) {
+        const int p = k * T + tid;
+        E *slot = s + px(p);
+        if ((u32)p < n) {
+          const unsigned sa = (unsigned)__cvta_generic_to_shared(slot);
+          if constexpr (sizeof(typename K::key_t) == 8)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa + K::key_off), "l"(keys + p) : "memory");
+          else
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa + K::key_off), "l"(keys + p) : "memory");
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa + K::val_off), "l"(vals + p) : "memory");
+        } else {
+          *slot = K::top();
+        }
+      }
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      sync();
+#pragma unroll
+      for (int k = 0; k < R; k++) {
+        const int p = tid * R + k;
+        E e = s[px(p)];
+        if ((u32)p < n) {
+          obs(*reinterpret_cast<const typename K::key_t *>(reinterpret_cast<const char *>(&e) + K::key_off),
+              *reinterpret_cast<const u32 *>(reinterpret_cast<const char *>(&e) + K::val_off));
+          e = K::raw(e);
+          s[px(p)] = e;
+        }
+        x[k] = e;
+      }
+      sync();
+      return;
+    }
 #pragma unroll
     for (int k = 0; k < R; k++) {
       const int p = k * T + tid;

@@ -62,6 +62,11 @@ struct KT<DT_U32> {
   static constexpr int key_words = 1;
   static constexpr bool lossy = false;
   static constexpr bool top_is_value = true;  // top() is bit-identical to any element equal to it
+  // Loaded by asynchronous copies: the key's and the val's bytes land at
+  // these offsets of the element, which raw() then completes in place.
+  static constexpr bool async_load = true;
+  static constexpr int key_off = 4, val_off = 0;  // (little-endian: key << 32 | val)
+  __device__ __forceinline__ static elem_t raw(elem_t e) { return e; }
   __device__ __forceinline__ static bool exact(key_t) { return true; }
   __device__ __forceinline__ static ord_t ord_key(key_t k) { return k; }
   __device__ __forceinline__ static key_t pad_key() { return 0xffffffffu; }
@@ -82,6 +87,9 @@ struct KT<DT_F32> {
   static constexpr int key_words = 1;
   static constexpr bool lossy = false;
   static constexpr bool top_is_value = false;  // an element may equal top() in order but carry other key bits
+  static constexpr bool async_load = false;
+  static constexpr int key_off = 0, val_off = 0;
+  __device__ __forceinline__ static elem_t raw(elem_t e) { return e; }
   __device__ __forceinline__ static bool exact(key_t) { return true; }
   __device__ __forceinline__ static ord_t ord_key(key_t k) { return f32_ordinal(k); }
   __device__ __forceinline__ static key_t pad_key() { return 0xffffffffu; }  // a NaN: ordinal max
@@ -116,6 +124,11 @@ struct KT<DT_F32W> {
   static constexpr int key_words = 1;
   static constexpr bool lossy = true;
   static constexpr bool top_is_value = true;  // top() is bit-identical to any element equal to it
+  static constexpr bool async_load = true;    // the key's bits, then raw() makes them the ordinal
+  static constexpr int key_off = 4, val_off = 0;
+  __device__ __forceinline__ static elem_t raw(elem_t e) {
+    return ((u64)f32_ordinal((u32)(e >> 32)) << 32) | (u32)e;  // (top() stays top())
+  }
   __device__ __forceinline__ static bool exact(key_t k) { return (k & 0x7fffffffu) <= 0x7f800000u; }
   __device__ __forceinline__ static ord_t ord_key(key_t k) { return f32_ordinal(k); }
   __device__ __forceinline__ static key_t pad_key() { return 0xffffffffu; }
@@ -136,6 +149,9 @@ struct KT<DT_U64> {
   static constexpr int key_words = 2;
   static constexpr bool lossy = false;
   static constexpr bool top_is_value = true;  // top() is bit-identical to any element equal to it
+  static constexpr bool async_load = true;    // (pad is left as it is: no comparison reads it)
+  static constexpr int key_off = 0, val_off = 8;
+  __device__ __forceinline__ static elem_t raw(elem_t e) { return e; }
   __device__ __forceinline__ static bool exact(key_t) { return true; }
   __device__ __forceinline__ static ord_t ord_key(key_t k) { return k; }
   __device__ __forceinline__ static key_t pad_key() { return ~0ull; }
