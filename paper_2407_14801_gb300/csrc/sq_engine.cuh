@@ -307,6 +307,10 @@ struct Engine {
         const size_t smem_tags = sizeof(SkewTagSmem<DT, CAP_T>);
         SQ_TRY(set_smem(k_skew_tags<DT, CAP_T>, smem_tags));
         k_skew_tags<DT, CAP_T><<<grid_skew_tags, 32 * SQ_SKEW_WARPS, smem_tags, st>>>(cp, ready);
+        SQ_TRY(cudaGetLastError());
+        L.end();
+        L.begin(KF_SKEW);
+        k_copy_runs<DT><<<nsm * 4, 256, 0, st>>>(cp);  // (returns at once when no run was queued)
       } else {
         SQ_TRY(set_smem(k_skew<DT, SKEW_CAP, false>, smem_skew));
         k_skew<DT, SKEW_CAP, false><<<grid_skew, 256, smem_skew, st>>>(cp, ready);
@@ -473,8 +477,8 @@ struct Engine {
     u32 leaf_cap[kLeafClasses];
     u64 ready_cap, fresh_cap, node_cap, meta_cap;
     size_t o_inst, o_leaves[2][kLeafClasses], o_ready[2], o_fresh[2], o_cnt, o_status, o_meta, o_done, o_trace,
-        o_wbase, o_fix, o_ctx;
-    u64 fix_cap;
+        o_wbase, o_fix, o_runs, o_ctx;
+    u64 fix_cap, runs_cap;
     size_t slab_bytes;
   };
 
@@ -534,6 +538,10 @@ struct Engine {
     if (kFix)
       for (int c = 0; c < kLeafClasses; c++) P.fix_cap += P.leaf_cap[c];
     P.o_fix = carve(sizeof(Leaf) * (size_t)P.fix_cap);
+    // run copies of big SkewTranspose tiles (a full list only makes the
+    // SkewTranspose copy its runs itself)
+    P.runs_cap = skew_only ? 0 : std::min<u64>(total_n / 256 + 4096, 0xffffffffull);
+    P.o_runs = carve(sizeof(RunCopy) * (size_t)P.runs_cap);
     P.o_ctx = carve(2 * sizeof(Ctx));
     P.slab_bytes = off;
     return P;
@@ -634,6 +642,8 @@ struct Engine {
     c.wbase = (u32 *)(slab + o_wbase);
     c.fix = (Leaf *)(slab + P.o_fix);
     c.fix_cap = (u32)std::min<u64>(P.fix_cap, 0xffffffffull);
+    c.runs = (RunCopy *)(slab + P.o_runs);
+    c.runs_cap = (u32)P.runs_cap;
     c.fresh_cap = (u32)fresh_cap;
     c.status = (Status *)(slab + o_status);
     c.meta = (u32 *)(slab + o_meta);
@@ -1004,6 +1014,8 @@ struct Engine {
       c.wbase = (u32 *)(slab + P.o_wbase);
       c.fix = (Leaf *)(slab + P.o_fix);
       c.fix_cap = (u32)std::min<u64>(P.fix_cap, 0xffffffffull);
+      c.runs = (RunCopy *)(slab + P.o_runs);
+      c.runs_cap = (u32)P.runs_cap;
       c.fresh_cap = (u32)P.fresh_cap;
       c.status = (Status *)(slab + P.o_status);
       c.meta = (u32 *)(slab + P.o_meta);

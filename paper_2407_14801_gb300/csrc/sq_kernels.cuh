@@ -1288,6 +1288,31 @@ static __device__ __noinline__ u32 skew_tag_run(const u32 *seg_start, const u32 
   }
   return cs + (hi - p);
 }
+// Queues the run [cs, rend) of a big tile's stream, dest d0 on, as one
+// RunCopy per column piece (lane l: the l-th column the run touches).  False
+// (nothing to copy queued) when the list has no room: the caller copies the
+// run.  Reserved slots left unused hold empty copies.
+static __device__ __noinline__ bool queue_run(const Ctx &c, const Node &nd, const u32 *seg_start, const u32 *seg_pre,
+                                              u32 nc, u32 cs, u32 rend, u32 d0, int lane) {
+  const u32 c0 = skew_col_of(seg_pre, nc, cs), c1 = skew_col_of(seg_pre, nc, rend - 1);
+  const u32 np = c1 - c0 + 1;  // <= kSkewCols
+  u32 base = 0;
+  if (lane == 0) base = atomicAdd(&c.status->runs_count, np);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  const bool fits = (u64)base + np <= c.runs_cap && (u64)d0 + (rend - cs) <= nd.n;
+  if ((u32)lane < np && base + lane < c.runs_cap) {
+    const u32 ci = c0 + lane;
+    const u32 qa = max(cs, seg_pre[ci]), qb = min(rend, seg_pre[ci + 1]);
+    RunCopy r;
+    r.src = nd.off + seg_start[ci] + (qa - seg_pre[ci]);
+    r.dst = nd.off + d0 + (qa - cs);
+    r.n = fits && qb > qa ? qb - qa : 0u;
+    r.inst = nd.inst;
+    c.runs[base + lane] = r;
+  }
+  return fits;
+}
+
 // Copies the run [cs, rend) of the tile's stream to dest d0 on, in order.
 template <class key_t, int NW>
 __device__ __noinline__ void skew_copy_run(const u32 *seg_start, const u32 *seg_pre, u32 nc, u32 cs, u32 rend, u32 d0,
@@ -1333,7 +1358,7 @@ struct SkewTagSmem {
   u32 base[kSkewBkts], running[kSkewBkts], ob[kSkewBkts + 1], adj[kSkewBkts];
   u32 seg_start[kSkewCols], seg_pre[kSkewCols + 1];
   uint8_t seg_t0[kSkewCols], seg_t1[kSkewCols];  // a big tile's column segments: first and last tag (0xff: empty)
-  u32 s_u, s_ri, s_S, s_big;
+  u32 s_u, s_ri, s_S, s_big, s_queued;
 };
 
 template <int DT, int CAP>
@@ -1416,15 +1441,24 @@ __global__ void __launch_bounds__(32 * SQ_SKEW_WARPS, 32 / SQ_SKEW_WARPS) k_skew
     for (int i = tid; i < kSkewBkts * (NW + 1); i += 32 * NW) sm.cnt[i] = 0;
     __syncthreads();
     for (u32 cs = 0; cs < S;) {
-      if (sm.s_big) {  // a long run of one tag is copied straight to its bucket
+      if (sm.s_big) {  // a long run of one tag goes straight to its bucket
         const u32 rend = skew_tag_run(sm.seg_start, sm.seg_pre, sm.seg_t0, sm.seg_t1, nc, cs, tg, lane);
         const u32 c0 = skew_col_of(sm.seg_pre, nc, cs);
         const u32 tS = tg[sm.seg_start[c0] + (cs - sm.seg_pre[c0])];
         if (tS < nk && rend - cs >= kSkewRunMin) {
-          skew_copy_run<key_t, NW>(sm.seg_start, sm.seg_pre, nc, cs, rend, sm.base[tS] + sm.running[tS], nd.n, dk, dv,
-                                   ak, av, &c.status->error, tid);
-          __syncthreads();  // running[tS] read everywhere
+          const u32 d0 = sm.base[tS] + sm.running[tS];
+          // warp 0 hands the run's column pieces to k_copy_runs, which copies
+          // them with every SM (a tile's runs would otherwise be copied by
+          // this CTA alone); if the list is full, the CTA copies the run here
+          if (warp == 0) {
+            const bool q = queue_run(c, nd, sm.seg_start, sm.seg_pre, nc, cs, rend, d0, lane);
+            if (lane == 0) sm.s_queued = q;
+          }
+          __syncthreads();  // (also: running[tS] read everywhere)
           if (tid == 0) sm.running[tS] += rend - cs;
+          if (!sm.s_queued)
+            skew_copy_run<key_t, NW>(sm.seg_start, sm.seg_pre, nc, cs, rend, d0, nd.n, dk, dv, ak, av,
+                                     &c.status->error, tid);
           __syncthreads();
           cs = rend;
           continue;
@@ -1608,6 +1642,50 @@ static __device__ void spawn_batch(const Ctx &c, bool has, const Child &ch, u32 
   __syncthreads();
 }
 
+// The run copies queued by this round's SkewTranspose (D -> A): every warp
+// takes the next one and copies it, eight loads in flight per lane.
+template <int DT>
+__global__ void __launch_bounds__(256) k_copy_runs(const Ctx *__restrict__ cp) {
+  const Ctx &c = *cp;
+  typedef typename KT<DT>::key_t key_t;
+  const u32 count = min(c.status->runs_count, c.runs_cap);
+  if (count == 0) return;
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    u32 i = 0;
+    if (lane == 0) i = atomicAdd(&c.status->runs_cursor, 1u);
+    i = __shfl_sync(0xffffffffu, i, 0);
+    if (i >= count) break;
+    const RunCopy r = c.runs[i];
+    const Inst I = c.inst[r.inst];
+    const key_t *dk = (const key_t *)I.dkeys + r.src;
+    const u32 *dv = I.dvals + r.src;
+    key_t *ak = (key_t *)I.keys + r.dst;
+    u32 *av = I.vals + r.dst;
+    constexpr int U = 8;
+    for (u32 qb = 0; qb < r.n; qb += U * 32) {
+      key_t kk[U];
+      u32 vv[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const u32 q = qb + (u32)(u * 32 + lane);
+        if (q < r.n) {
+          kk[u] = dk[q];
+          vv[u] = dv[q];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const u32 q = qb + (u32)(u * 32 + lane);
+        if (q < r.n) {
+          ak[q] = kk[u];
+          av[q] = vv[u];
+        }
+      }
+    }
+  }
+}
+
 // Bucket children of every ready node (Algorithm 1's last loop), spawned in
 // work items of kExpandChunk buckets.  Every bucket of a SquareSort node is
 // non-empty (bucket j >= 1 holds pivot j, bucket 0 the minimum), so the node
@@ -1701,7 +1779,7 @@ static __global__ void k_round_begin(const Ctx *__restrict__ cp) {
   u32 *z = reinterpret_cast<u32 *>(c.cnt_nxt);
   for (u32 i = threadIdx.x; i < nc; i += blockDim.x) z[i] = 0;
   u32 *cur = &c.status->cur_count;
-  if (threadIdx.x < 7 + kLeafClasses) cur[threadIdx.x] = 0;
+  if (threadIdx.x < kRoundCursors) cur[threadIdx.x] = 0;
 }
 
 // Totals of a graph-launched run (a host-driven run counts on the host).

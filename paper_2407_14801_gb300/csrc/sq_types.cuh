@@ -278,6 +278,15 @@ struct Status {
   // the leaf cursors of graph-launched rounds)
   u32 cur_count, cur_scan, cur_skew, cur_expand, cur_ebkt, cur_fix, fix_count;
   u32 cur_leaf[kLeafClasses];
+  u32 runs_count, runs_cursor;  // this round's run copies (RunCopy list)
+};
+constexpr int kRoundCursors = 7 + kLeafClasses + 2;  // Status words from cur_count on, zeroed every round
+
+// One column's piece of a run of one bucket tag in a big SkewTranspose tile:
+// n elements from D at src to A at dst (element offsets in the instance).
+struct RunCopy {
+  u64 src, dst;
+  u32 n, inst;
 };
 
 // A trace record, one per recursing node (written when its pivots are chosen).
@@ -323,6 +332,8 @@ struct Ctx {
   u32 class_cap[kLeafClasses];  // max elements per leaf class
   int recurse;                  // 0 for a stand-alone SkewTranspose
   u32 ninst;                    // instances of the run
+  RunCopy *runs;                // run copies the SkewTranspose hands to k_copy_runs
+  u32 runs_cap;
 };
 
 // Metadata layout of a ready node (32-bit words from Node::meta), each
