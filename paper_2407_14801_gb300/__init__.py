@@ -202,14 +202,56 @@ def sq_skew_transpose_noalloc(keys_in, vals_in, rows: int, cols: int, pivot_keys
 skew_transpose_noalloc = sq_skew_transpose_noalloc
 
 
+# sq_sort_desc as a numpy record (keys, vals, n, dtype, 4 bytes of padding,
+# seed): a batch's descriptors are built as one array rather than field by
+# field through ctypes (4096 instances: a few ms less per call).
+_DESC_DTYPE = None
+_DTYPE_CODE = {}
+
+
+def _desc_dtype():
+    global _DESC_DTYPE
+    if _DESC_DTYPE is None:
+        import numpy as np
+
+        _DESC_DTYPE = np.dtype([("keys", "<u8"), ("vals", "<u8"), ("n", "<u8"), ("dtype", "<i4"), ("pad", "<i4"),
+                                ("seed", "<u8")])
+        assert _DESC_DTYPE.itemsize == ctypes.sizeof(SortDesc)
+    return _DESC_DTYPE
+
+
+def _addr(t):
+    if t is None:
+        return 0
+    return t.data_ptr() if hasattr(t, "data_ptr") else t.ctypes.data  # numpy
+
+
+def _code(t):
+    c = _DTYPE_CODE.get(t.dtype)
+    if c is None:
+        c = _DTYPE_CODE[t.dtype] = _dtype_of(t, None)
+    return c
+
+
 def sq_sort_batch(items, stream=None):
     """Sort many independent instances together.  items: iterable of
     (keys, vals_or_None, seed) CUDA tensors; each is sorted in place."""
+    import numpy as np
+
     items = list(items)
-    descs = (SortDesc * max(len(items), 1))()
-    for i, (k, v, seed) in enumerate(items):
-        descs[i] = SortDesc(_ptr(k), _ptr(v), _numel(k), _dtype_of(k, None), seed & (2**64 - 1))
-    _check(lib().sq_sort_batch(descs, len(items), _stream(stream)))
+    mask = 2**64 - 1
+    code = _DTYPE_CODE
+    rows = []
+    try:
+        for k, v, seed in items:  # tensors (the common case, kept lean)
+            c = code.get(k.dtype)
+            if c is None:
+                c = _code(k)
+            rows.append((k.data_ptr(), 0 if v is None else v.data_ptr(), k.numel(), c, 0, seed & mask))
+    except AttributeError:  # numpy arrays among them
+        rows = [(_addr(k), _addr(v), _numel(k), _code(k), 0, seed & mask) for k, v, seed in items]
+    descs = np.array(rows or [(0, 0, 0, 0, 0, 0)], dtype=_desc_dtype())
+    _check(lib().sq_sort_batch(descs.ctypes.data_as(ctypes.POINTER(SortDesc)), len(items), _stream(stream)))
 
 
 sort_batch = sq_sort_batch
