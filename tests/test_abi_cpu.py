@@ -71,3 +71,39 @@ def test_launch_mode_without_a_device(sq):
     assert L.sq_set_launch_mode(5) == 1 and b"launch mode" in L.sq_last_error()
     assert L.sq_set_launch_mode(0) == 0 and L.sq_get_launch_mode() == 0
     assert L.sq_set_launch_mode(2) == 0
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every structure the binding passes through the C ABI (ctypes, and the
+    numpy records of batch descriptors) lays its fields out exactly as the C
+    compiler does for the header's struct."""
+    import shutil
+    import subprocess
+
+    import paper_2407_14801_gb300 as sq
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pairs = [(sq.TraceRec, "sq_trace_rec"), (sq.SortOpts, "sq_sort_opts"), (sq.SkewBuf, "sq_skew_buf"),
+             (sq.SortDesc, "sq_sort_desc"), (sq.ServeOpts, "sq_serve_opts"), (sq.Stats, "sq_stats")]
+    lines = []
+    for cls, cname in pairs:
+        fields = [f for f, _ in cls._fields_]
+        fmt = " ".join(["%zu"] * (1 + len(fields)))
+        args = ", ".join([f"sizeof({cname})"] + [f"offsetof({cname}, {f})" for f in fields])
+        lines.append(f'  printf("{fmt}\\n", {args});')
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "squaresort.h"\nint main(void) {\n' +
+                   "\n".join(lines) + "\n  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()
+    for (cls, cname), line in zip(pairs, out):
+        got = list(map(int, line.split()))
+        want = [ctypes.sizeof(cls)] + [getattr(cls, f).offset for f, _ in cls._fields_]
+        assert got == want, (cname, got, want)
+    rec = sq._desc_dtype()  # the batch descriptors' numpy record
+    desc = list(map(int, out[3].split()))
+    assert rec.itemsize == desc[0]
+    assert [rec.fields[f][1] for f, _ in sq.SortDesc._fields_] == desc[1:]
