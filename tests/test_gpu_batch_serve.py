@@ -216,3 +216,107 @@ def test_serve_admits_while_others_run(sq):
     assert (reqs[1][0] == np.sort(small_k)).all()
     assert (reqs[0][0] == np.sort(big_k)).all()
     assert (reqs[0][0] == big_k[reqs[0][1].view(np.uint32)]).all()
+
+
+# ------------------------------------------------- the stated workload sizes --
+
+def _segmented_unique_result(src, keys, vals, offs, dtype):
+    """check_unique_result over many instances laid end to end: within every
+    instance the output is non-decreasing by (ordinal(key), val), its payloads
+    are a permutation of 0..n_i-1, and each key is the original key of its
+    payload -- which together pin the unique sorted result of each."""
+    from test_gpu_fullsize import ordinal64
+
+    total = keys.numel()
+    dev = keys.device
+    sizes = offs[1:] - offs[:-1]
+    inst = torch.repeat_interleave(torch.arange(sizes.numel(), device=dev), sizes)
+    v = vals.to(torch.int64) & 0xFFFFFFFF
+    o = ordinal64(keys, dtype)
+    start = torch.zeros(total, dtype=torch.bool, device=dev)
+    start[offs[:-1][sizes > 0]] = True
+    ok = (o[1:] > o[:-1]) | ((o[1:] == o[:-1]) & (v[1:] > v[:-1])) | start[1:]
+    assert bool(ok.all()), "an instance is not sorted by (key, val)"
+    del ok, o
+    assert bool((v < sizes[inst]).all()), "a payload is out of its instance's range"
+    g = offs[:-1][inst] + v
+    seen = torch.zeros(total, dtype=torch.bool, device=dev)
+    seen[g] = True
+    assert bool(seen.all()), "payloads are not a permutation within each instance"
+    assert bool((src[g] == keys).all()), "a key left its payload"
+
+
+def test_batch_config_4096_instances_2e8_to_2e20(sq):
+    """The batched workload at its stated size: 4096 uint32 instances of
+    sizes log-uniform in [2^8, 2^20] (size seed 7), uniform keys, index
+    payload, all in one sq_sort_batch at the default cutoffs.  Every
+    instance is checked on the device by the unique-result properties, and
+    64 of them -- the largest among them -- element by element against the
+    oracle."""
+    count = 4096
+    sizes = W.batch_sizes(count, 7)
+    offs_np = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    total = int(offs_np[-1])
+    flat = np.empty(total, dtype=np.uint32)
+    for i in range(count):
+        flat[offs_np[i]:offs_np[i + 1]] = W.uniform_u32(int(sizes[i]), (7 << 20) + i + 1)
+    src = torch.from_numpy(flat.view(np.int32)).cuda()
+    keys = src.clone()
+    offs = torch.from_numpy(offs_np).cuda()
+    inst = torch.repeat_interleave(torch.arange(count, device="cuda"), offs[1:] - offs[:-1])
+    vals = (torch.arange(total, device="cuda") - offs[:-1][inst]).to(torch.int32)
+    del inst
+    seeds = [7 + i for i in range(count)]
+    sq.sort_batch([(keys[offs_np[i]:offs_np[i + 1]], vals[offs_np[i]:offs_np[i + 1]], seeds[i])
+                   for i in range(count)])
+    torch.cuda.synchronize()
+    _segmented_unique_result(src, keys, vals, offs, "u32")
+    big = int(np.argmax(sizes))
+    pick = [big] + [i for i in range(0, count, 64) if i != big][:63]
+    assert len(pick) == 64
+    gk = keys.cpu().numpy().view(np.uint32)
+    gv = vals.cpu().numpy().view(np.uint32)
+    for i in pick:
+        a, b = offs_np[i], offs_np[i + 1]
+        ek, ev, _, _ = oracle.sort(flat[a:b], W.iota(b - a), seed=seeds[i], cutoff=sq.cutoff_for("u32", b - a))
+        assert (gk[a:b] == ek).all() and (gv[a:b] == ev).all(), i
+
+
+def test_serve_config_sizes_2e10_to_2e24_all_key_types(sq):
+    """The served workload's request mix: sizes log-uniform in [2^10, 2^24]
+    and key types uniform over uint32 / uint64 / float32 with their
+    workload generators (uniform, Zipf(1.1), N(0,1) with specials), drawn as
+    the request stream draws them, plus one 2^24 request and one 2^10
+    request of each key type, all in flight together under the 16 GB budget.
+    Requests up to 2^18 keys are compared with the oracle element by
+    element; larger ones by the unique-result properties on the device."""
+    stream = W.serve_requests(36, 5, rate_per_s=1.0)
+    specs = [(n, dt, s) for (_, n, dt, s) in stream]
+    specs += [(1 << 24, dt, 900 + i) for i, dt in enumerate(("u64", "f32", "u32"))]
+    specs += [(1 << 10, dt, 910 + i) for i, dt in enumerate(("u64", "f32", "u32"))]
+    reqs = []
+    for n, dt, s in specs:
+        k = W.keys_for(dt, n, s)
+        reqs.append((k, W.iota(n), dt, s))
+    srcs = [r[0].copy() for r in reqs]
+    res = serve_all(sq, reqs, budget=16 << 30, cutoff=0)
+    n_oracle = n_props = 0
+    for (st, lat), (k, v, dt, s), src in zip(res, reqs, srcs):
+        assert st == 0 and lat > 0
+        if k.size <= (1 << 18):
+            ek, ev = expected(src, W.iota(k.size), dt, s, sq.cutoff_for(dt, k.size))
+            assert same(k, ek, dt) and (v == ev).all(), (k.size, dt, s)
+            n_oracle += 1
+        else:
+            from test_gpu_fullsize import check_unique_result
+
+            tv = VIEW[dt]
+            sb = torch.from_numpy(src.view(tv)).cuda()
+            ob = torch.from_numpy(k.view(tv)).cuda()
+            ov = torch.from_numpy(v.view(np.int32)).cuda()
+            if dt == "f32":
+                sb, ob = sb.view(torch.int32), ob.view(torch.int32)
+            check_unique_result(sb, ob, ov, dt)
+            n_props += 1
+    assert n_oracle >= 10 and n_props >= 6
+    assert {dt for (n, dt, _) in specs if n == 1 << 24} == {"u32", "u64", "f32"}
