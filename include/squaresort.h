@@ -119,18 +119,23 @@ sq_status sq_skew_transpose(const sq_skew_buf *buf, uint64_t rows, uint64_t cols
  * they need the permutation -- a process whose frameworks already hold the
  * whole device in their own caching pools, or a latency-critical path that
  * must not call cudaMalloc / cudaFree (they can synchronise the device or
- * fail under memory pressure).  Same arguments, results and errors as
- * sq_skew_transpose; all scratch (per-node metadata, work lists, status
- * words) comes from one 64 MiB array that the library holds in device memory
- * on every GPU that loads it, until the process exits.  Shapes whose scratch
- * exceeds 64 MiB (about 0.078 * k * cols + 2 * (k + cols) 32-bit words, e.g.
- * beyond roughly 14000 x 14000 with k = cols) are refused with
- * SQ_ERR_INVALID and a message naming the size.  The first call on a device
- * looks up the array's device address (with that device current); make that
- * first call before any stream capture.  Every call uses the same array and
- * leaves the previous call's contents behind (the call initialises what it
- * reads): calls whose GPU work overlaps -- on different streams or from
- * different threads -- race on it and must be serialised by the caller. */
+ * fail under memory pressure).  Same arguments, results, errors and error
+ * messages as sq_skew_transpose; all scratch (per-node metadata, work lists,
+ * status words) comes from one 64 MiB array in device memory.  The array is
+ * reserved on a device by the first call made there (that call loads the
+ * part of the library that holds it), and stays reserved until the process
+ * exits; so make one call on each device at start-up, before other pools
+ * fill it and before any stream capture.  If that first reservation fails
+ * the call returns SQ_ERR_CUDA and leaves no CUDA error pending.  Shapes
+ * whose scratch exceeds 64 MiB (about 0.078 * k * cols + 2 * (k + cols)
+ * 32-bit words, e.g. beyond roughly 14000 x 14000 with k = cols) are refused
+ * with SQ_ERR_INVALID and a message naming the size.  Every call uses the
+ * same array and leaves the previous call's contents behind (the call
+ * initialises what it reads): calls whose GPU work overlaps -- on different
+ * streams or from different threads -- race on it and must be serialised by
+ * the caller.  Unlike sq_skew_transpose, which allocates a one-byte bucket
+ * tag per element for its counting-sort kernel, this form runs the
+ * SkewTranspose kernel that searches the pivots itself. */
 sq_status sq_skew_transpose_noalloc(const sq_skew_buf *buf, uint64_t rows, uint64_t cols, sq_stream_t stream);
 
 /* One instance of a batched sort: device buffers, sorted in place. */

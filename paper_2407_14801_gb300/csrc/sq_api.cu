@@ -194,6 +194,26 @@ sq_status sort_device(void *keys, uint32_t *vals, uint64_t n, sq_dtype dtype, ui
 
 namespace sq {
 void api_set_error(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
+// Argument checks of the stand-alone SkewTranspose entry points: clears the
+// calling thread's error message, then returns SQ_OK or the first failure
+// (with its message set).
+sq_status api_check_skew_args(const sq_skew_buf *buf, uint64_t rows, uint64_t cols) {
+  g_err[0] = 0;
+  if (!buf) return fail(SQ_ERR_INVALID, "buf is NULL");
+  if (!dtype_ok(buf->dtype)) return fail(SQ_ERR_INVALID, "bad dtype %d", (int)buf->dtype);
+  const uint64_t n = buf->n, k = buf->k;
+  if (rows == 0 || cols == 0 || n > rows * cols || n >= (1ull << 32) || rows >= (1ull << 32) ||
+      cols >= (1ull << 32))
+    return fail(SQ_ERR_INVALID, "bad shape: n=%llu rows=%llu cols=%llu", (unsigned long long)n,
+                (unsigned long long)rows, (unsigned long long)cols);
+  if (k == 0 || k > (uint64_t)engine_max_pivots(buf->dtype) + 1)
+    return fail(SQ_ERR_INVALID, "k = %llu outside [1, %u]", (unsigned long long)k, engine_max_pivots(buf->dtype) + 1);
+  if (!buf->bucket_start_out || (n && (!buf->keys_in || !buf->vals_in || !buf->keys_out || !buf->vals_out)) ||
+      (k > 1 && (!buf->pivot_keys || !buf->pivot_vals)))
+    return fail(SQ_ERR_INVALID, "null buffer");
+  return SQ_OK;
+}
 }  // namespace sq
 
 extern "C" {
@@ -310,20 +330,9 @@ sq_status sq_sort(void *keys, uint32_t *vals, uint64_t n, sq_dtype dtype, uint64
 }
 
 sq_status sq_skew_transpose(const sq_skew_buf *buf, uint64_t rows, uint64_t cols, sq_stream_t stream) {
-  g_err[0] = 0;
-  if (!buf) return fail(SQ_ERR_INVALID, "buf is NULL");
-  if (!dtype_ok(buf->dtype)) return fail(SQ_ERR_INVALID, "bad dtype %d", (int)buf->dtype);
+  const sq_status chk = sq::api_check_skew_args(buf, rows, cols);
+  if (chk != SQ_OK) return chk;
   const uint64_t n = buf->n, k = buf->k;
-  if (rows == 0 || cols == 0 || n > rows * cols || n >= (1ull << 32) || rows >= (1ull << 32) ||
-      cols >= (1ull << 32))
-    return fail(SQ_ERR_INVALID, "bad shape: n=%llu rows=%llu cols=%llu", (unsigned long long)n,
-                (unsigned long long)rows, (unsigned long long)cols);
-  if (k == 0 || k > (uint64_t)sq::engine_max_pivots(buf->dtype) + 1)
-    return fail(SQ_ERR_INVALID, "k = %llu outside [1, %u]", (unsigned long long)k,
-                sq::engine_max_pivots(buf->dtype) + 1);
-  if (!buf->bucket_start_out || (n && (!buf->keys_in || !buf->vals_in || !buf->keys_out || !buf->vals_out)) ||
-      (k > 1 && (!buf->pivot_keys || !buf->pivot_vals)))
-    return fail(SQ_ERR_INVALID, "null buffer");
   sq::InstSpec is{};
   is.keys = buf->keys_out;
   is.vals = buf->vals_out;

@@ -7,25 +7,20 @@
 // under memory pressure at an arbitrary moment).  This entry point does the
 // same work as sq_skew_transpose but takes all its scratch (the per-node
 // metadata, work lists and status words) from one statically sized device
-// array that the library carries from the moment it is loaded.
+// array.  The array belongs to this file's module, which the CUDA runtime
+// loads (and so reserves the array) on the first call on each device.
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 
 #include "../../include/squaresort.h"
 #include "sq_engine.h"
 
 namespace {
 
-// Scratch shared by every call on a device.  Every GPU that loads this
-// library holds it until the process exits.
+// Scratch shared by every call on a device.  Reserved on a device by the
+// first call there; held until the process exits.
 constexpr size_t kNoAllocScratchBytes = 64ull << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
-
-// Device address of the array, looked up once per device (host code only
-// sees a host-side stand-in under the array's name).
-std::mutex g_mu;
-void *g_scratch_ptr[128] = {};
 
 struct Bump {
   char *base;
@@ -49,19 +44,16 @@ sq_status nfail(sq_status s, const char *msg) {
 
 }  // namespace
 
+namespace sq {
+sq_status api_check_skew_args(const sq_skew_buf *buf, uint64_t rows, uint64_t cols);  // (sq_api.cu)
+}
+
 extern "C" sq_status sq_skew_transpose_noalloc(const sq_skew_buf *buf, uint64_t rows, uint64_t cols,
                                                 sq_stream_t stream) {
   char msg[256];
-  if (!buf) return nfail(SQ_ERR_INVALID, "buf is NULL");
-  if (buf->dtype < 0 || buf->dtype > 2) return nfail(SQ_ERR_INVALID, "bad dtype");
+  const sq_status chk = sq::api_check_skew_args(buf, rows, cols);  // the regular call's checks and messages
+  if (chk != SQ_OK) return chk;
   const uint64_t n = buf->n, k = buf->k;
-  if (rows == 0 || cols == 0 || n > rows * cols || n >= (1ull << 32) || rows >= (1ull << 32) ||
-      cols >= (1ull << 32))
-    return nfail(SQ_ERR_INVALID, "bad shape");
-  if (k == 0 || k > (uint64_t)sq::engine_max_pivots(buf->dtype) + 1) return nfail(SQ_ERR_INVALID, "bad k");
-  if (!buf->bucket_start_out || (n && (!buf->keys_in || !buf->vals_in || !buf->keys_out || !buf->vals_out)) ||
-      (k > 1 && (!buf->pivot_keys || !buf->pivot_vals)))
-    return nfail(SQ_ERR_INVALID, "null buffer");
   const uint64_t need = sq::engine_skew_scratch_bytes(buf->dtype, n, cols, k);
   if (need > kNoAllocScratchBytes) {
     snprintf(msg, sizeof(msg),
@@ -70,21 +62,17 @@ extern "C" sq_status sq_skew_transpose_noalloc(const sq_skew_buf *buf, uint64_t 
              (unsigned long long)need, (unsigned long long)kNoAllocScratchBytes);
     return nfail(SQ_ERR_INVALID, msg);
   }
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= 128) return nfail(SQ_ERR_CUDA, "cudaGetDevice failed");
+  // The array's device address in the current device's context.  Host code
+  // sees only a host-side stand-in under the array's name, so the address is
+  // asked for on every call (cheap once the module is loaded; no address is
+  // kept across a device reset or a context change).  On a device's first
+  // call this loads the module, which is where the array is reserved.
   void *base = nullptr;
-  {
-    std::lock_guard<std::mutex> g(g_mu);
-    if (!g_scratch_ptr[dev]) {  // first call on this device (current device)
-      e = cudaGetSymbolAddress(&g_scratch_ptr[dev], g_noalloc_scratch);
-      if (e != cudaSuccess) {
-        g_scratch_ptr[dev] = nullptr;
-        snprintf(msg, sizeof(msg), "cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-        return nfail(SQ_ERR_CUDA, msg);
-      }
-    }
-    base = g_scratch_ptr[dev];
+  cudaError_t e = cudaGetSymbolAddress(&base, g_noalloc_scratch);
+  if (e != cudaSuccess || !base) {
+    cudaGetLastError();  // leave no stale error for the next, unrelated runtime check
+    snprintf(msg, sizeof(msg), "cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+    return nfail(SQ_ERR_CUDA, msg);
   }
   Bump bump{static_cast<char *>(base), kNoAllocScratchBytes, 0};
   alignas(64) unsigned char readback[512];

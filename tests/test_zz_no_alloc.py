@@ -94,3 +94,52 @@ def test_noalloc_refuses_oversized_shapes(sq):
     st = sq.lib().sq_skew_transpose_noalloc(ctypes.byref(buf), rows, cols, None)
     assert st == 1  # SQ_ERR_INVALID, before any device work
     assert b"scratch" in sq.lib().sq_last_error()
+
+
+def _default_pool():
+    """The current device's default stream-ordered memory pool, through the
+    CUDA driver API (the pool every cudaMallocAsync without a pool uses)."""
+    cu = ctypes.CDLL("libcuda.so.1")
+    dev = ctypes.c_int(0)
+    assert cu.cuDeviceGet(ctypes.byref(dev), torch.cuda.current_device()) == 0
+    pool = ctypes.c_void_p()
+    assert cu.cuDeviceGetDefaultMemPool(ctypes.byref(pool), dev) == 0
+    return cu, pool
+
+
+USED_MEM_CURRENT, USED_MEM_HIGH = 7, 8  # CUmemPool_attribute values
+
+
+def _pool_attr(cu, pool, attr):
+    v = ctypes.c_uint64(0)
+    assert cu.cuMemPoolGetAttribute(pool, attr, ctypes.byref(v)) == 0
+    return v.value
+
+
+def test_noalloc_takes_nothing_from_the_stream_ordered_pool(sq):
+    """What the entry point exists for: a warm call draws no memory from the
+    device's default pool (where the regular call's stream-ordered scratch
+    comes from).  The pool's high watermark is reset before the call and
+    must not rise above the pool's use at that moment."""
+    rows, cols, n, k = 2048, 2048, 4194000, 2048
+    keys, vals, pk, pv = make_case(rows, cols, n, k, "u32", seed=5)
+    dev = lambda a, v: torch.from_numpy(np.ascontiguousarray(a).view(v).copy()).cuda()
+    dev_in = (dev(keys, np.int32), dev(vals, np.int32), dev(pk, np.int32), dev(pv, np.int32))
+    ref = run(sq.skew_transpose, dev_in, rows, cols, k, "u32")
+    cu, pool = _default_pool()
+    used_high_regular = None
+    run(sq.skew_transpose_noalloc, dev_in, rows, cols, k, "u32")  # warm: the array is reserved here
+    torch.cuda.synchronize()
+    for fn in (sq.skew_transpose, sq.skew_transpose_noalloc):
+        used0 = _pool_attr(cu, pool, USED_MEM_CURRENT)
+        zero = ctypes.c_uint64(0)
+        assert cu.cuMemPoolSetAttribute(pool, USED_MEM_HIGH, ctypes.byref(zero)) == 0
+        got = run(fn, dev_in, rows, cols, k, "u32")
+        high = _pool_attr(cu, pool, USED_MEM_HIGH)
+        if fn is sq.skew_transpose:
+            used_high_regular = high - used0  # the check below can see an allocation
+        else:
+            assert high <= used0, f"the allocation-free call drew {high - used0} bytes from the pool"
+        for a, b in zip(got, ref):
+            assert (a == b).all()
+    assert used_high_regular > 0
