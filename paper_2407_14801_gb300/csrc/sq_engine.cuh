@@ -170,7 +170,27 @@ struct Engine {
     return e;
   }
 
+  // Leaves of 32-bit key ordinals (uint32, float32) take the radix base case
+  // in the classes where it is faster than the merge sort.
+  static constexpr bool kRadix = sizeof(EL) == 8 && KL::top_is_value;
+
+  template <int T, int R>
+  static cudaError_t launch_leaf_radix(Launcher &L, const Ctx *cp, int cls, u32 count, int nsm) {
+    const size_t smem = radix_leaf_bytes<LDT, T, R>();
+    auto kern = k_leaf_radix<LDT, T, R>;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    const u32 grid = count == kDev ? fill_grid(kern, T, smem, nsm) : count;
+    L.begin(KF_LEAF);
+    kern<<<grid, T, smem, L.st>>>(cp, cls, count);
+    L.end();
+    return cudaGetLastError();
+  }
+
   static cudaError_t launch_leaf_class(Launcher &L, const Ctx *cp, int cls, u32 count, int nsm) {
+    if constexpr (kRadix) {
+      if (cls == 4) return launch_leaf_radix<512, 32>(L, cp, 4, count, nsm);
+    }
     switch (cls) {
       case 0: return launch_leaf<32, 2, true>(L, cp, 0, count, nsm);
       case 1: return launch_leaf<32, 16, true>(L, cp, 1, count, nsm);

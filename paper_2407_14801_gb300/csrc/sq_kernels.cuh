@@ -17,6 +17,7 @@
 // A leaf finishing decrements its parent's pending count; the last column
 // makes the parent ready for the next round, the last bucket completes it.
 #pragma once
+#include "sq_radix.cuh"
 #include "sq_sorter.cuh"
 
 namespace sq {
@@ -271,6 +272,17 @@ __host__ __device__ constexpr size_t leaf_sort_bytes() {
   return (size_t)(WARP ? 8 : 1) * Sorter<KT<DT>, T, R, WARP>::SMEM * sizeof(typename KT<DT>::elem_t);
 }
 
+// Shared memory of a radix leaf CTA: the sort's element slots, the NaN list
+// (float32 keys), then the radix counters and scratch.
+template <int DT, int T, int R>
+__host__ __device__ constexpr size_t radix_ws_offset() {
+  return (leaf_sort_bytes<DT, T, R, false>() + (KT<DT>::lossy ? 4 * kNanWords : 0) + 15) & ~(size_t)15;
+}
+template <int DT, int T, int R>
+__host__ __device__ constexpr size_t radix_leaf_bytes() {
+  return radix_ws_offset<DT, T, R>() + RadixLeaf<KT<DT>, T, R>::kBytes;
+}
+
 // A leaf whose ascending runs descend (Sorter::runs) is moved run by run:
 // every output position, in coalesced order, takes its element from the
 // loaded copy in s.  Returns false (nothing written) if the runs do not
@@ -405,6 +417,121 @@ __global__ void __launch_bounds__(WARP ? 256 : T, kLeafMinBlocks<DT, T, WARP>())
       if (nn && (pre != 1 || moves)) {  // (a sorted leaf left in place kept its bits)
         for (u32 i = tid; i < nn; i += T) ok[L.n - nn + nan_rank(nl, nn, nl[1 + i], i)] = (key_t)nl[1 + kNanCap + i];
         S::sync();
+      }
+    }
+    if (tid == 0) {
+      __threadfence();
+      child_done(c, L.parent, L.flags & 0xffu, L.inst);
+    }
+  }
+}
+
+// The merge sort of a leaf whose radix order failed the (key, val) check
+// (equal keys whose vals do not ascend in input order): the leaf is taken
+// from s (blocked layout) and put back there sorted.  Out of line and fed
+// through shared memory, so that the radix path keeps its registers (an
+// array passed by reference to a call would live in local memory).
+template <class S>
+__device__ __noinline__ void leaf_merge_fallback(typename S::E *s, int tid) {
+  typename S::E x[S::R];
+#pragma unroll
+  for (int k = 0; k < S::R; k++) x[k] = s[S::px(tid * S::R + k)];
+  __syncthreads();
+  S::sort(x, s, tid);
+#pragma unroll
+  for (int k = 0; k < S::R; k++) s[S::px(tid * S::R + k)] = x[k];
+  __syncthreads();
+}
+
+// A leaf of the radix class: one CTA of T threads x R elements, loaded and
+// checked for presorted input as in k_leaf, then sorted by RadixLeaf (or
+// merge sorted when the radix order is not the (key, val) order).  Leaves
+// of 32-bit key ordinals only (uint32, float32 one-word elements).
+template <int DT, int T, int R>
+__global__ void __launch_bounds__(T, 1) k_leaf_radix(const Ctx *__restrict__ cp, int cls, u32 count) {
+  const Ctx &c = *cp;
+  typedef KT<DT> K;
+  typedef Sorter<K, T, R, false> S;
+  typedef RadixLeaf<K, T, R> RL;
+  typedef typename K::elem_t E;
+  typedef typename K::key_t key_t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  E *s = reinterpret_cast<E *>(smem_raw);
+  u32 *nl = reinterpret_cast<u32 *>(smem_raw + leaf_sort_bytes<DT, T, R, false>());  // K::lossy only
+  u32 *ws = reinterpret_cast<u32 *>(smem_raw + radix_ws_offset<DT, T, R>());
+  const int tid = threadIdx.x;
+  const bool dyn = count == kDev;  // a fixed-size grid: every CTA takes the next leaf
+  const u32 cnt = dyn ? min(c.cnt_cur->leaves[cls], c.leaf_cap[cls]) : count;
+  __shared__ u32 s_li;
+  __shared__ u32 s_pre[S::kPreWords];
+  __shared__ u32 s_run[S::kRunWords];
+  __shared__ typename S::RunInfo s_ri[T];
+  auto next_leaf = [&](u32 done_li) -> u32 {
+    if (!dyn) return done_li == kNone ? blockIdx.x : cnt;  // one leaf per CTA
+    if (tid == 0) s_li = atomicAdd(&c.status->cur_leaf[cls], 1u);
+    __syncthreads();
+    const u32 li = s_li;
+    __syncthreads();
+    return li;
+  };
+  for (u32 li = next_leaf(kNone); li < cnt; li = next_leaf(li)) {
+    const Leaf L = c.leaves_cur[cls][li];
+    const Inst I = c.inst[L.inst];
+    E x[R];
+    const u32 out = (L.flags >> 8) & 0xffu;
+    const bool from_src = (L.flags & LEAF_SRC) != 0;
+    const key_t *ik = (const key_t *)(from_src ? I.skeys : I.keys) + L.off;
+    const u32 *iv = (from_src ? I.svals : I.vals) + L.off;
+    key_t *ok = (key_t *)(out ? I.dkeys : I.fkeys) + L.off;
+    u32 *ov = (out ? I.dvals : I.fvals) + L.off;
+    const bool moves = (const void *)ik != (const void *)ok || iv != ov;  // else sorted in place
+    u32 nn = 0;
+    if constexpr (K::lossy) {
+      if (tid == 0) nl[0] = 0;
+      __syncthreads();
+    }
+    S::load(x, s, tid, ik, iv, L.n, [&](key_t k, u32 v) { nan_note<K>(nl, k, v); });
+    if constexpr (K::lossy) {
+      nn = nl[0];
+      __syncthreads();  // read before the list is reset for the next leaf
+      if (nn > kNanCap) {  // too many to restore: the fix list's exact (key, val) sort takes the leaf
+        if (moves)
+          for (u32 p = tid; p < L.n; p += T) {
+            ok[p] = ik[p];
+            ov[p] = iv[p];
+          }
+        if (tid == 0) push_fix(c, L);
+        continue;
+      }
+    }
+    // (the presorted test and the runs read the leaf from s: x is reloaded
+    // afterwards, so that it holds no registers meanwhile)
+    u32 rot = 0;
+    int pre = S::presorted_s(s, tid, L.n, s_pre, rot);
+    if (pre == 4) {  // runs in descending order: every element straight to its place, else sorted
+      if (!leaf_runs<S>(s, tid, L.n, s_run, s_ri, ok, ov)) pre = 0;
+      __syncthreads();  // (the moved leaf is written before its NaNs get their bits back)
+    }
+#pragma unroll
+    for (int k = 0; k < R; k++) x[k] = s[S::px(tid * R + k)];
+    if (pre == 0 && !RL::sort(x, s, tid, L.n, ws)) {  // (RL::sort ends with a barrier: s is free)
+#pragma unroll
+      for (int k = 0; k < R; k++) s[S::px(tid * R + k)] = x[k];
+      __syncthreads();
+      leaf_merge_fallback<S>(s, tid);
+#pragma unroll
+      for (int k = 0; k < R; k++) x[k] = s[S::px(tid * R + k)];
+      __syncthreads();
+    }
+    if (pre < 4 && (pre != 1 || moves)) {  // (a sorted leaf in place is left as it is)
+      const int n = (int)L.n, r = pre == 3 ? (int)rot : 0;
+      const bool rev = pre == 2;
+      S::store_mapped(x, s, tid, ok, ov, L.n, [&](int i) { return rev ? n - 1 - i : (i >= r ? i - r : i + n - r); });
+    }
+    if constexpr (K::lossy) {
+      if (nn && (pre != 1 || moves)) {  // (a sorted leaf left in place kept its bits)
+        for (u32 i = tid; i < nn; i += T) ok[L.n - nn + nan_rank(nl, nn, nl[1 + i], i)] = (key_t)nl[1 + kNanCap + i];
+        __syncthreads();
       }
     }
     if (tid == 0) {

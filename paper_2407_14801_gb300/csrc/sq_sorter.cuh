@@ -12,6 +12,8 @@
 #pragma once
 #include <cooperative_groups.h>
 
+#include <type_traits>
+
 #include "sq_types.cuh"
 
 namespace sq {
@@ -272,7 +274,17 @@ struct Sorter {
   // passed).
   static constexpr int kPreWords = WARP ? 1 : 2 * (T / 32);
   static constexpr u32 kFewRuns = 32;
-  static_assert(R < 32, "a thread's descents fit one mask word");
+  static_assert(R <= 64, "a thread's descents fit one mask word");
+  // A thread's descents as a bit mask (bit k: a descent after its element k).
+  typedef typename std::conditional<(R < 32), u32, u64>::type mask_t;
+  static constexpr u32 kMaskBits = 8 * sizeof(mask_t);
+  __device__ __forceinline__ static u32 mclz(mask_t m) {
+    if constexpr (sizeof(mask_t) == 8) return (u32)__clzll((long long)m); else return (u32)__clz((int)m);
+  }
+  __device__ __forceinline__ static u32 mffs(mask_t m) {
+    if constexpr (sizeof(mask_t) == 8) return (u32)__ffsll((long long)m); else return (u32)__ffs((int)m);
+  }
+  __device__ __forceinline__ static mask_t below(int k) { return (mask_t(1) << k) - mask_t(1); }  // bits [0, k)
   __device__ __forceinline__ static int classify(u32 n, u32 d, bool wrap) {
     if (n < 2 || d == 0) return 1;
     if (d == n - 1) return 2;
@@ -298,11 +310,24 @@ struct Sorter {
     first = __reduce_min_sync(0xffffffffu, first);
   }
   __device__ static int presorted(E (&x)[R], E *s, int tid, u32 n, u32 *w, u32 &p) {
+    u32 d, first;
+    descents(x, s, tid, n, d, first);
+    return presorted_tail(s, tid, n, w, p, d, first);
+  }
+  // The same, the thread's elements read from s (x need not be live).
+  __device__ static int presorted_s(const E *s, int tid, u32 n, u32 *w, u32 &p) {
+    const mask_t m = desc_mask(s, tid, n);
+    u32 d = (u32)__popcll((unsigned long long)m);
+    u32 first = m ? (u32)(tid * R) + mffs(m) - 1u : 0xffffffffu;
+    d = __reduce_add_sync(0xffffffffu, d);
+    first = __reduce_min_sync(0xffffffffu, first);
+    return presorted_tail(s, tid, n, w, p, d, first);
+  }
+  // d, first: the warp's descents and first descent.
+  __device__ static int presorted_tail(const E *s, int tid, u32 n, u32 *w, u32 &p, u32 d, u32 first) {
     // (s is read only before the barrier: once past it, other threads may
     // already be writing the sorted or moved leaf into s)
     const bool wrap = n >= 2 && !K::lt(s[px(0)], s[px((int)n - 1)]);
-    u32 d, first;
-    descents(x, s, tid, n, d, first);
     if (!WARP) {
       if ((tid & 31) == 0) {
         w[2 * (tid >> 5)] = d;
@@ -327,39 +352,39 @@ struct Sorter {
   // end of the run holding its last).
   // (The runs test reads the loaded leaf from s only, so that x is free
   // meanwhile.)
-  __device__ static u32 desc_mask(const E *s, int tid, u32 n) {
-    u32 m = 0;
+  __device__ static mask_t desc_mask(const E *s, int tid, u32 n) {
+    mask_t m = 0;
     E cur = s[px(tid * R)];
 #pragma unroll
     for (int k = 0; k < R; k++) {
       const u32 i = (u32)(tid * R + k);
       if (i + 1 < n) {
         const E nx = s[px(tid * R + k + 1)];
-        if (K::lt(nx, cur)) m |= 1u << k;
+        if (K::lt(nx, cur)) m |= mask_t(1) << k;
         cur = nx;
       }
     }
     return m;
   }
   // b and e of the element at base + k
-  __device__ __forceinline__ static u32 run_b(u32 m, int k, u32 base, u32 pre) {
-    const u32 lb = m & ((1u << k) - 1u);  // the descents before it
-    return lb ? base + 32u - (u32)__clz((int)lb) : pre;
+  __device__ __forceinline__ static u32 run_b(mask_t m, int k, u32 base, u32 pre) {
+    const mask_t lb = m & below(k);  // the descents before it
+    return lb ? base + kMaskBits - mclz(lb) : pre;
   }
-  __device__ __forceinline__ static u32 run_e(u32 m, int k, u32 base, u32 suf) {
-    const u32 hb = m & ~((1u << k) - 1u);  // the descents at or after it
-    return hb ? base + (u32)__ffs((int)hb) : suf;
+  __device__ __forceinline__ static u32 run_e(mask_t m, int k, u32 base, u32 suf) {
+    const mask_t hb = m & ~below(k);  // the descents at or after it (k <= R < kMaskBits)
+    return hb ? base + mffs(hb) : suf;
   }
   // pre and suf for every thread of the group from the masks: the largest
   // run start of the earlier threads (lo if none) and the smallest run end
   // of the later ones (hi if none); tmax and tmin: the group's own largest
   // run start and smallest run end.  w: kRunWords of shared memory.
   static constexpr int kRunWords = WARP ? 1 : 2 * (T / 32);
-  __device__ static void run_scan(u32 m, u32 base, int tid, u32 lo, u32 hi, u32 *w, u32 &pre, u32 &suf, u32 &tmax,
+  __device__ static void run_scan(mask_t m, u32 base, int tid, u32 lo, u32 hi, u32 *w, u32 &pre, u32 &suf, u32 &tmax,
                                   u32 &tmin) {
     const int lane = tid & 31;
-    u32 a = m ? base + 32u - (u32)__clz((int)m) : lo;  // the start of the thread's last run
-    u32 z = m ? base + (u32)__ffs((int)m) : hi;        // the end of its first run
+    u32 a = m ? base + kMaskBits - mclz(m) : lo;  // the start of the thread's last run
+    u32 z = m ? base + mffs(m) : hi;              // the end of its first run
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const u32 ta = __shfl_up_sync(0xffffffffu, a, o);
@@ -397,11 +422,11 @@ struct Sorter {
   // no higher than the run before it, [b, d+1), starts (x[e-1] <= x[b]).
   // at(p): the element at leaf position p.
   template <class At>
-  __device__ static bool runs_descend(u32 m, u32 base, u32 pre, u32 suf, At at) {
+  __device__ static bool runs_descend(mask_t m, u32 base, u32 pre, u32 suf, At at) {
     bool ok = true;
 #pragma unroll
     for (int k = 0; k < R; k++)
-      if (m >> k & 1u) {
+      if (m >> k & mask_t(1)) {
         const u32 b = run_b(m, k, base, pre), e = run_e(m, k + 1, base, suf);
         if (K::lt(at(b), at(e - 1))) ok = false;
       }
@@ -409,12 +434,13 @@ struct Sorter {
   }
   // A thread's runs, kept for the move.
   struct RunInfo {
-    u32 m, pre, suf;
+    mask_t m;
+    u32 pre, suf;
   };
   // The runs test for a group holding the whole leaf; ri[tid] gets this
   // thread's runs (read by the others after the test's closing barrier).
   __device__ static bool runs(const E *s, int tid, u32 n, u32 *w, RunInfo *ri) {
-    const u32 m = desc_mask(s, tid, n);
+    const mask_t m = desc_mask(s, tid, n);
     const u32 base = (u32)(tid * R);
     u32 pre, suf, tmax, tmin;
     run_scan(m, base, tid, 0u, n, w, pre, suf, tmax, tmin);
@@ -512,9 +538,9 @@ struct ClusterSorter {
     const int rank = (int)cl.block_rank();
     const u32 q0 = (u32)rank * NC;
     const u32 nr = n > q0 ? min((u32)NC, n - q0) : 0u;
-    u32 m = S::desc_mask(s, tid, nr);
+    typename S::mask_t m = S::desc_mask(s, tid, nr);
     if (tid == T - 1 && q0 + NC < n && K::lt(cl.map_shared_rank(w, rank + 1)->head, s[S::px(NC - 1)]))
-      m |= 1u << (R - 1);  // the descent into the next part
+      m |= typename S::mask_t(1) << (R - 1);  // the descent into the next part
     const u32 base = q0 + (u32)(tid * R);
     u32 pre, suf, tmax, tmin;
     S::run_scan(m, base, tid, 0u, n, w->wr, pre, suf, tmax, tmin);
