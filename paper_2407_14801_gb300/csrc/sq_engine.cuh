@@ -187,9 +187,31 @@ struct Engine {
     return cudaGetLastError();
   }
 
+  template <int T, int R, int G>
+  static cudaError_t launch_leaf_radix_cluster(Launcher &L, const Ctx *cp, int cls, u32 count, int nsm) {
+    const size_t smem = radix_leaf_bytes<LDT, T, R>();
+    auto kern = k_leaf_radix_cluster<LDT, T, R, G>;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    const u32 grid = count == kDev ? fill_clusters(kern, T, smem, G, nsm) : count * G;
+    L.begin(KF_LEAF);
+    e = launch_cluster(kern, dim3(grid, 1, 1), T, smem, G, L.st, cp, cls, count);
+    L.end();
+    return e;
+  }
+
   static cudaError_t launch_leaf_class(Launcher &L, const Ctx *cp, int cls, u32 count, int nsm) {
     if constexpr (kRadix) {
-      if (cls == 4) return launch_leaf_radix<512, 32>(L, cp, 4, count, nsm);
+      switch (cls) {  // (class c holds (c - 2) * 8192 elements: 16K, 24K, 32K, ... 64K)
+        case 4: return launch_leaf_radix<512, 32>(L, cp, 4, count, nsm);
+        case 5:
+        case 6: return launch_leaf_radix_cluster<512, 32, 2>(L, cp, cls, count, nsm);
+        case 7:
+        case 8: return launch_leaf_radix_cluster<512, 32, 3>(L, cp, cls, count, nsm);
+        case 9:
+        case 10: return launch_leaf_radix_cluster<512, 32, 4>(L, cp, cls, count, nsm);
+        default: break;
+      }
     }
     switch (cls) {
       case 0: return launch_leaf<32, 2, true>(L, cp, 0, count, nsm);

@@ -426,6 +426,24 @@ __global__ void __launch_bounds__(WARP ? 256 : T, kLeafMinBlocks<DT, T, WARP>())
   }
 }
 
+// Stores the first n elements of a group's s (already in output order),
+// coalesced; ends with a barrier.
+template <class S>
+__device__ __forceinline__ void store_from_s(const typename S::E *s, int tid, typename S::K::key_t *keys, u32 *vals,
+                                             u32 n) {
+  constexpr int T = S::N / S::R;
+#pragma unroll
+  for (int k = 0; k < S::R; k++) {
+    const int p = k * T + tid;
+    if ((u32)p < n) {
+      const typename S::E e = s[S::px(p)];
+      keys[p] = S::K::key(e);
+      vals[p] = S::K::val(e);
+    }
+  }
+  __syncthreads();
+}
+
 // The merge sort of a leaf whose radix order failed the (key, val) check
 // (equal keys whose vals do not ascend in input order): the leaf is taken
 // from s (blocked layout) and put back there sorted.  Out of line and fed
@@ -512,18 +530,21 @@ __global__ void __launch_bounds__(T, 1) k_leaf_radix(const Ctx *__restrict__ cp,
       if (!leaf_runs<S>(s, tid, L.n, s_run, s_ri, ok, ov)) pre = 0;
       __syncthreads();  // (the moved leaf is written before its NaNs get their bits back)
     }
-#pragma unroll
-    for (int k = 0; k < R; k++) x[k] = s[S::px(tid * R + k)];
-    if (pre == 0 && !RL::sort(x, s, tid, L.n, ws)) {  // (RL::sort ends with a barrier: s is free)
-#pragma unroll
-      for (int k = 0; k < R; k++) s[S::px(tid * R + k)] = x[k];
-      __syncthreads();
-      leaf_merge_fallback<S>(s, tid);
+    if (pre == 1) {  // sorted: s holds the leaf in order (a sorted leaf in place is left as it is)
+      if (moves) store_from_s<S>(s, tid, ok, ov, L.n);
+    } else if (pre != 4) {
 #pragma unroll
       for (int k = 0; k < R; k++) x[k] = s[S::px(tid * R + k)];
-      __syncthreads();
-    }
-    if (pre < 4 && (pre != 1 || moves)) {  // (a sorted leaf in place is left as it is)
+      __syncthreads();  // every thread holds its elements before any writes s (the sort, or the moved store)
+      if (pre == 0 && !RL::sort(x, s, tid, L.n, ws)) {  // (RL::sort ends with a barrier: s is free)
+#pragma unroll
+        for (int k = 0; k < R; k++) s[S::px(tid * R + k)] = x[k];
+        __syncthreads();
+        leaf_merge_fallback<S>(s, tid);
+#pragma unroll
+        for (int k = 0; k < R; k++) x[k] = s[S::px(tid * R + k)];
+        __syncthreads();
+      }
       const int n = (int)L.n, r = pre == 3 ? (int)rot : 0;
       const bool rev = pre == 2;
       S::store_mapped(x, s, tid, ok, ov, L.n, [&](int i) { return rev ? n - 1 - i : (i >= r ? i - r : i + n - r); });
@@ -625,6 +646,134 @@ __global__ void __launch_bounds__(T, (T <= 512 && sizeof(typename KT<DT>::elem_t
     if (pre <= 1) {
       if (pre == 0) CS::sort(x, s, tid, (int)L.n);
       if (pre == 0 || moves) S::store(x, s, tid, ok + q0, ov + q0, nr);  // a sorted leaf in place stays
+    }
+    cl.sync();  // (also: no part changes before every CTA has read what it moves)
+    if constexpr (K::lossy) {
+      if (total && (pre != 1 || moves)) {  // the leaf's NaNs end it, in val order (then by part, entry)
+        for (u32 i = tid; i < nn; i += T) {
+          const u32 v = nl[1 + i];
+          u32 r = 0;
+          for (int q = 0; q < G; q++) {
+            const u32 *ql = cl.map_shared_rank(nl, q);
+            const u32 qn = ql[0];
+            for (u32 j = 0; j < qn; j++) {
+              const u32 vj = ql[1 + j];
+              r += (vj < v) || (vj == v && (q < rank || (q == rank && j < i)));
+            }
+          }
+          ok[L.n - total + r] = (key_t)nl[1 + kNanCap + i];
+        }
+        cl.sync();  // the lists are read before the next leaf resets them
+      }
+    }
+    if (rank == 0 && tid == 0) {
+      __threadfence();
+      child_done(c, L.parent, L.flags & 0xffu, L.inst);
+    }
+  }
+}
+
+// A leaf of a radix cluster class: CTA `rank` of the cluster loads
+// positions [rank*NC, (rank+1)*NC) of the leaf (NC = T*R); the presorted
+// test and the moves of k_leaf_cluster, else every CTA sorts its part with
+// RadixLeaf (merge sorting it instead when the radix order is not the
+// (key, val) order) and the parts are merged by the cluster's staged
+// cross-CTA merge rounds (ClusterSorter::merge_rounds).
+template <int DT, int T, int R, int G>
+__global__ void __launch_bounds__(T, 1) k_leaf_radix_cluster(const Ctx *__restrict__ cp, int cls, u32 count) {
+  const Ctx &c = *cp;
+  typedef KT<DT> K;
+  typedef ClusterSorter<K, T, R, G> CS;
+  typedef typename CS::S S;
+  typedef RadixLeaf<K, T, R> RL;
+  typedef typename K::elem_t E;
+  typedef typename K::key_t key_t;
+  namespace cg = cooperative_groups;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  E *s = reinterpret_cast<E *>(smem_raw);
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const bool dyn = count == kDev;  // a fixed-size grid: every cluster takes the next leaf
+  const u32 cnt = dyn ? min(c.cnt_cur->leaves[cls], c.leaf_cap[cls]) : count;
+  const int tid = threadIdx.x;
+  u32 *nl = reinterpret_cast<u32 *>(smem_raw + leaf_sort_bytes<DT, T, R, false>());  // K::lossy only: this part's NaNs
+  u32 *ws = reinterpret_cast<u32 *>(smem_raw + radix_ws_offset<DT, T, R>());
+  __shared__ u32 s_li;
+  __shared__ typename CS::PreW s_pre;
+  auto next_leaf = [&](u32 done_li) -> u32 {
+    if (!dyn) return done_li == kNone ? blockIdx.x / G : cnt;  // one leaf per cluster
+    if (rank == 0 && tid == 0) s_li = atomicAdd(&c.status->cur_leaf[cls], 1u);
+    cl.sync();
+    const u32 li = *cl.map_shared_rank(&s_li, 0);
+    cl.sync();  // read everywhere before rank 0 takes the next
+    return li;
+  };
+  for (u32 li = next_leaf(kNone); li < cnt; li = next_leaf(li)) {  // the whole cluster
+    const Leaf L = c.leaves_cur[cls][li];
+    const Inst I = c.inst[L.inst];
+    const u32 nr = L.n > (u32)rank * CS::NC ? min((u32)CS::NC, L.n - (u32)rank * CS::NC) : 0u;
+    const u32 out = (L.flags >> 8) & 0xffu;
+    const bool from_src = (L.flags & LEAF_SRC) != 0;
+    const key_t *ik = (const key_t *)(from_src ? I.skeys : I.keys) + L.off;
+    const u32 *iv = (from_src ? I.svals : I.vals) + L.off;
+    key_t *ok = (key_t *)(out ? I.dkeys : I.fkeys) + L.off;
+    u32 *ov = (out ? I.dvals : I.fvals) + L.off;
+    const bool moves = (const void *)ik != (const void *)ok || iv != ov;  // else sorted in place
+    const u32 q0 = (u32)rank * CS::NC;  // this CTA's part of the leaf: [q0, q0 + nr)
+    E x[R];
+    u32 nn = 0, total = 0;
+    if constexpr (K::lossy) {
+      if (tid == 0) nl[0] = 0;
+      __syncthreads();
+    }
+    S::load(x, s, tid, ik + q0, iv + q0, nr, [&](key_t k, u32 v) { nan_note<K>(nl, k, v); });
+    if constexpr (K::lossy) {
+      cl.sync();  // every part's list is complete
+      u32 most = 0;
+      for (int r = 0; r < G; r++) {
+        const u32 m = *cl.map_shared_rank(nl, r);
+        total += m;
+        most = max(most, m);
+      }
+      nn = nl[0];
+      cl.sync();  // the counts are read before any list changes
+      if (most > kNanCap) {  // too many to restore: the fix list's exact (key, val) sort takes the leaf
+        if (moves)
+          for (u32 p = tid; p < nr; p += T) {
+            ok[q0 + p] = ik[q0 + p];
+            ov[q0 + p] = iv[q0 + p];
+          }
+        cl.sync();
+        if (rank == 0 && tid == 0) push_fix(c, L);
+        continue;
+      }
+    }
+    // (the presorted test and the moves read the leaf from shared memory; x
+    // is reloaded afterwards, so that it holds no registers meanwhile)
+    u32 rot = 0;
+    int pre = CS::presorted_s(s, tid, L.n, &s_pre, rot);
+    if (pre >= 2) {  // reversed, rotated, or runs in descending order (if they pass the test): moved
+      if (!leaf_move_cluster<CS>(s, tid, L.n, pre, rot, &s_pre, ok, ov)) pre = 0;
+    }
+    if (pre == 1) {  // sorted: s holds this part in order (a sorted leaf in place stays)
+      if (moves) store_from_s<S>(s, tid, ok + q0, ov + q0, nr);
+    } else if (pre == 0) {
+#pragma unroll
+      for (int k = 0; k < R; k++) x[k] = s[S::px(tid * R + k)];
+      {
+        cl.sync();  // every CTA has read what it moves or tests in the others' parts
+        if (!RL::sort(x, s, tid, nr, ws)) {  // this part only (RL::sort ends with a barrier: s is free)
+#pragma unroll
+          for (int k = 0; k < R; k++) s[S::px(tid * R + k)] = x[k];
+          __syncthreads();
+          leaf_merge_fallback<S>(s, tid);
+#pragma unroll
+          for (int k = 0; k < R; k++) x[k] = s[S::px(tid * R + k)];
+          __syncthreads();
+        }
+        CS::merge_rounds(x, s, tid, (int)L.n);
+      }
+      S::store(x, s, tid, ok + q0, ov + q0, nr);
     }
     cl.sync();  // (also: no part changes before every CTA has read what it moves)
     if constexpr (K::lossy) {

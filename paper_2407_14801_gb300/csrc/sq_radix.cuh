@@ -197,4 +197,5 @@ struct RadixLeaf {
   }
 };
 
+
 }  // namespace sq

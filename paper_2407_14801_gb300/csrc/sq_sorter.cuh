@@ -486,13 +486,32 @@ struct ClusterSorter {
     typename S::RunInfo ri[T];
   };
   __device__ static int presorted(E (&x)[R], E *s, int tid, u32 n, PreW *w, u32 &p) {
+    const int rank = (int)cooperative_groups::this_cluster().block_rank();
+    const u32 q0 = (u32)rank * NC;
+    const u32 nr = n > q0 ? min((u32)NC, n - q0) : 0u;
+    u32 d, first;
+    S::descents(x, s, tid, nr, d, first);
+    return presorted_tail(s, tid, n, w, p, d, first);
+  }
+  // The same, the thread's elements read from s (x need not be live).
+  __device__ static int presorted_s(const E *s, int tid, u32 n, PreW *w, u32 &p) {
+    const int rank = (int)cooperative_groups::this_cluster().block_rank();
+    const u32 q0 = (u32)rank * NC;
+    const u32 nr = n > q0 ? min((u32)NC, n - q0) : 0u;
+    const typename S::mask_t m = S::desc_mask(s, tid, nr);
+    u32 d = (u32)__popcll((unsigned long long)m);
+    u32 first = m ? (u32)(tid * R) + S::mffs(m) - 1u : 0xffffffffu;
+    d = __reduce_add_sync(0xffffffffu, d);
+    first = __reduce_min_sync(0xffffffffu, first);
+    return presorted_tail(s, tid, n, w, p, d, first);
+  }
+  // d, first: the warp's descents and first descent within this CTA's part.
+  __device__ static int presorted_tail(const E *s, int tid, u32 n, PreW *w, u32 &p, u32 d, u32 first) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const u32 q0 = (u32)rank * NC;
     const u32 nr = n > q0 ? min((u32)NC, n - q0) : 0u;
-    u32 d, first;
-    S::descents(x, s, tid, nr, d, first);
     if ((tid & 31) == 0) {
       w->wd[2 * (tid >> 5)] = d;
       w->wd[2 * (tid >> 5) + 1] = first;
