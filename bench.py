@@ -121,6 +121,45 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+
+def make_clocks(local: int) -> "ClockSampler":
+    vis = [x for x in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if x.strip()]
+    return ClockSampler(int(vis[local]) if local < len(vis) and vis[local].strip().isdigit() else local)
+
+
+def profiled(sq, run):
+    """Runs run() once more with per-launch CUDA events on (outside every
+    timed region) and returns the library's statistics of that pass."""
+    import torch
+
+    torch.cuda.synchronize()
+    sq.reset_stats()
+    sq.set_profiling(True)
+    try:
+        run()
+        torch.cuda.synchronize()
+    finally:
+        sq.set_profiling(False)
+    return sq.stats()
+
+
+def roofline_of(st, workload_name: str, note: str):
+    """The dominant kernel family's achieved HBM bandwidth: its algorithmic
+    bytes per launch (counted on the device) over its average launch time."""
+    fams = [f for f in st["ms"] if st["launches"][f] > 0 and st["bytes"][f] > 0]
+    dom = max(fams, key=lambda f: st["ms"][f])
+    L = st["launches"][dom]
+    bytes_per_launch = st["bytes"][dom] / L
+    avg_ms = st["ms"][dom] / L
+    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    peak, peak_src = measured_peaks()
+    return {"bound": "hbm", "kernel": f"k_{dom}", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": profiled_traffic(dom, workload_name),
+            "peak_source": f"{peak_src} (copy bandwidth)", "algorithmic_bytes_per_launch": bytes_per_launch,
+            "avg_launch_ms": avg_ms, "launches": L, "measured_in": note,
+            "family_ms": {f: round(st["ms"][f], 3) for f in st["ms"] if st["launches"][f]}}
+
+
 # ------------------------------------------------------------- workloads --
 
 def make_inputs_u32(n: int, device, dists=DISTS):
@@ -206,9 +245,7 @@ def bench_plain(args, sq, dist, rank, world, local):
         sq.sort(keys[i], vals[i], seed=i, dtype="u32", cutoff=cutoff)
     torch.cuda.synchronize()
     sq.reset_stats()
-    sq.set_profiling(True)
-    vis = [x for x in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if x.strip()]
-    clocks = ClockSampler(int(vis[local]) if local < len(vis) and vis[local].strip().isdigit() else local)
+    clocks = make_clocks(local)
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     dist_mod = dist
@@ -225,32 +262,30 @@ def bench_plain(args, sq, dist, rank, world, local):
     t_wall = time.perf_counter() - t_wall0
     D.barrier(dist_mod)
     clk = clocks.stop()
-    sq.set_profiling(False)
-    st = sq.stats()
+    st_timed = sq.stats()
     ms = ev0.elapsed_time(ev1)
     ms_max = D.max_over_ranks(ms, dist_mod, dev)
     value = world * args.steps * n / (ms_max / 1e3) / 1e9
 
     # correctness of every timed step (outside the timed region)
     ok = all(check_sorted_u32(keys[i], vals[i], inputs[seq[i]]) for i in range(args.warmup, total))
+
+    # kernel-family split: the same sorts again on the same inputs, with
+    # per-launch CUDA events on (a pass of its own, not the timed one)
+    def again():
+        for i in range(args.warmup, total):
+            keys[i].copy_(inputs[seq[i]])
+            vals[i].copy_(iota)
+        torch.cuda.synchronize()
+        for i in range(args.warmup, total):
+            sq.sort(keys[i], vals[i], seed=i, dtype="u32", cutoff=cutoff)
+
+    st = profiled(sq, again)
     del keys, vals
     torch.cuda.empty_cache()
-
-    # roofline of the dominant kernel family (by summed launch time)
-    fams = [f for f in st["ms"] if st["launches"][f] > 0 and st["bytes"][f] > 0]
-    dom = max(fams, key=lambda f: st["ms"][f])
-    L = st["launches"][dom]
-    bytes_per_launch = st["bytes"][dom] / L
-    avg_ms = st["ms"][dom] / L
-    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
-    peak, peak_src = measured_peaks()
     workload_name = f"plain_u32_n{n}"
-    traffic = profiled_traffic(dom, workload_name)
-    roofline = {"bound": "hbm", "kernel": f"k_{dom}", "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                "peak_source": f"{peak_src} (copy bandwidth)", "algorithmic_bytes_per_launch": bytes_per_launch,
-                "avg_launch_ms": avg_ms, "launches": L,
-                "family_ms": {f: round(st["ms"][f], 3) for f in st["ms"] if st["launches"][f]}}
+    roofline = roofline_of(st, workload_name, "a profiling pass over the same sorts after the timed region")
+    peak = roofline["peak"]
     # whole-step roofline against the ideal one-level traffic 6 w n (w = 8 bytes)
     step_frac = (6 * 8 * n) / (ms_max / args.steps / 1e3) / 1e9 / peak
 
@@ -275,9 +310,9 @@ def bench_plain(args, sq, dist, rank, world, local):
         "roofline": roofline,
         "step_hbm_frac_ideal_6wn": round(step_frac, 4),
         "e2e": e2e,
-        "gpu_launches": int(sum(st["launches"].values())),
-        "rounds_per_step": st["rounds"] / max(1, args.steps),
-        "recursing_nodes_per_step": st["nodes"] / max(1, args.steps),
+        "gpu_launches": int(sum(st_timed["launches"].values())),
+        "rounds_per_step": st_timed["rounds"] / max(1, args.steps),
+        "recursing_nodes_per_step": st_timed["nodes"] / max(1, args.steps),
         "wall_s": round(t_wall, 4),
         "clocks": clk,
         "verified": ok,
@@ -337,9 +372,7 @@ def bench_wide(args, sq, dist, rank, world, local):
         step(i)
     torch.cuda.synchronize()
     sq.reset_stats()
-    sq.set_profiling(True)
-    vis = [x for x in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if x.strip()]
-    clocks = ClockSampler(int(vis[local]) if local < len(vis) and vis[local].strip().isdigit() else local)
+    clocks = make_clocks(local)
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     D.barrier(dist)
@@ -351,28 +384,28 @@ def bench_wide(args, sq, dist, rank, world, local):
     torch.cuda.synchronize()
     D.barrier(dist)
     clk = clocks.stop()
-    sq.set_profiling(False)
-    st = sq.stats()
+    st_timed = sq.stats()
     ms_max = D.max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     value = world * args.steps * 2 * n / (ms_max / 1e3) / 1e9
     bits = {"u64": lambda t: t, "f32": lambda t: t.view(torch.int32)}
     ok = all(check_sorted_any(bits[d](src[d]), bits[d](bufs[i][d][0]), bufs[i][d][1], d)
              for i in range(args.warmup, total) for d in src)
+
+    def again():
+        for i in range(args.warmup, total):
+            for d in src:
+                bufs[i][d][0].copy_(src[d])
+                bufs[i][d][1].copy_(iota)
+        torch.cuda.synchronize()
+        for i in range(args.warmup, total):
+            step(i)
+
+    st = profiled(sq, again)
     del bufs
     torch.cuda.empty_cache()
-    fams = [f for f in st["ms"] if st["launches"][f] > 0 and st["bytes"][f] > 0]
-    dom = max(fams, key=lambda f: st["ms"][f])
-    L = st["launches"][dom]
-    bytes_per_launch = st["bytes"][dom] / L
-    avg_ms = st["ms"][dom] / L
-    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
-    peak, peak_src = measured_peaks()
     workload_name = f"wide_u64_f32_n{n}"
-    roofline = {"bound": "hbm", "kernel": f"k_{dom}", "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": profiled_traffic(dom, workload_name),
-                "peak_source": f"{peak_src} (copy bandwidth)", "algorithmic_bytes_per_launch": bytes_per_launch,
-                "avg_launch_ms": avg_ms, "launches": L,
-                "family_ms": {f: round(st["ms"][f], 3) for f in st["ms"] if st["launches"][f]}}
+    roofline = roofline_of(st, workload_name, "a profiling pass over the same sorts after the timed region")
+    peak = roofline["peak"]
     step_frac = (6 * (12 + 8) * n) / (ms_max / args.steps / 1e3) / 1e9 / peak
     e2e = None
     if not args.no_e2e:
@@ -404,8 +437,8 @@ def bench_wide(args, sq, dist, rank, world, local):
                    "l2": "inputs larger than L2 (each step sorts its own copies)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline, "step_hbm_frac_ideal_6wn": round(step_frac, 4), "e2e": e2e,
-        "gpu_launches": int(sum(st["launches"].values())),
-        "rounds_per_step": st["rounds"] / max(1, args.steps), "clocks": clk, "verified": ok,
+        "gpu_launches": int(sum(st_timed["launches"].values())),
+        "rounds_per_step": st_timed["rounds"] / max(1, args.steps), "clocks": clk, "verified": ok,
     }
 
 
@@ -504,8 +537,12 @@ def run_ours(args):
             out["cpu_baseline"] = cpu_baseline_wide()
     elif args.workload == "batch":
         out = bench_batch(args, sq, dist, rank, world, local)
+        if rank == 0 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline_batch(args)
     elif args.workload == "serve":
         out = bench_serve(args, sq, dist, rank, world, local)
+        if rank == 0 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline_serve(args)
     else:
         raise SystemExit(f"unknown workload {args.workload}")
     if rank == 0:
@@ -519,7 +556,8 @@ def run_ours(args):
 def bench_batch(args, sq, dist, rank, world, local):
     """4096 independent uint32 instances, sizes log-uniform in [2^8, 2^20],
     uniform keys, index payload, seed 7: one sq_sort_batch call per step
-    against one sq_sort call per instance.  Ranks take disjoint shares."""
+    against one sq_sort call per instance.  Ranks take disjoint shares.
+    The instances lie end to end in one device buffer (each a view)."""
     import numpy as np
     import torch
 
@@ -530,29 +568,37 @@ def bench_batch(args, sq, dist, rank, world, local):
     count = args.batch_count
     sizes = W.batch_sizes(count, 7, args.batch_lo, args.batch_hi)
     mine = list(D.shard(count, rank, world))
-    src = [torch.from_numpy(W.uniform_u32(int(sizes[i]), (7 << 20) + i + 1).view(np.int32)).to(dev) for i in mine]
-    keys = [t.clone() for t in src]
-    vals = [torch.arange(t.numel(), dtype=torch.int32, device=dev) for t in src]
-    total_keys = int(sum(t.numel() for t in src))
+    my_sizes = [int(sizes[i]) for i in mine]
+    offs = np.concatenate([[0], np.cumsum(my_sizes)]).astype(np.int64)
+    total_keys = int(offs[-1])
+    flat = np.empty(total_keys, dtype=np.uint32)
+    for j, i in enumerate(mine):
+        flat[offs[j]:offs[j + 1]] = W.uniform_u32(my_sizes[j], (7 << 20) + i + 1)
+    src = torch.from_numpy(flat.view(np.int32)).to(dev)
+    iota = torch.cat([torch.arange(m, dtype=torch.int32, device=dev) for m in my_sizes]) if my_sizes else \
+        torch.empty(0, dtype=torch.int32, device=dev)
+    keys, vals = src.clone(), iota.clone()
+    views = [(keys[offs[j]:offs[j + 1]], vals[offs[j]:offs[j + 1]], 7 + i) for j, i in enumerate(mine)]
     stream = torch.cuda.current_stream()
 
     def restore():
-        for k, s0, v in zip(keys, src, vals):
-            k.copy_(s0)
-            v.copy_(torch.arange(v.numel(), dtype=torch.int32, device=dev))
+        keys.copy_(src)
+        vals.copy_(iota)
         torch.cuda.synchronize()
 
     def run_batched():
-        sq.sort_batch([(k, v, 7 + i) for i, (k, v) in enumerate(zip(keys, vals))])
+        sq.sort_batch(views)
 
     def run_single():
-        for i, (k, v) in enumerate(zip(keys, vals)):
-            sq.sort(k, v, seed=7 + i, dtype="u32")
+        for k, v, seed in views:
+            sq.sort(k, v, seed=seed, dtype="u32")
 
-    def timed(fn, steps, warm):
+    def timed(fn, steps, warm, clocks=None):
         for _ in range(warm):
             restore()
             fn()
+        if clocks is not None:
+            clocks.start()
         tot = 0.0
         for _ in range(steps):
             restore()
@@ -563,102 +609,348 @@ def bench_batch(args, sq, dist, rank, world, local):
             e1.record(stream)
             torch.cuda.synchronize()
             tot += e0.elapsed_time(e1)
-        return D.max_over_ranks(tot, dist, dev) / steps
+        clk = clocks.stop() if clocks is not None else None
+        return D.max_over_ranks(tot, dist, dev) / steps, clk
 
+    clocks = make_clocks(local)
     sq.reset_stats()
-    ms_b = timed(run_batched, args.steps, args.warmup)
-    st = sq.stats()
-    ms_s = None if args.batch_no_single else timed(run_single, max(1, args.steps // 4), 1)
-    # correctness of the last batched step is checked instance by instance
+    ms_b, clk = timed(run_batched, args.steps, args.warmup, clocks)
+    st_timed = sq.stats()
+    launches = sum(st_timed["launches"].values()) / max(1, args.steps + args.warmup)
+    ms_s = None if args.batch_no_single else timed(run_single, max(1, args.steps // 4), 1)[0]
+    # correctness of one batched step, every instance, on the device
     restore()
     run_batched()
-    ok = all(check_sorted_u32(k, v, s0) for k, v, s0 in zip(keys, vals, src))
+    torch.cuda.synchronize()
+    ok = all(check_sorted_u32(k, v, src[offs[j]:offs[j + 1]]) for j, (k, v, _) in enumerate(views))
+
+    def again():
+        restore()
+        run_batched()
+
+    st = profiled(sq, again)
+    workload_name = f"batch_u32_{count}_instances_2^{args.batch_lo}..2^{args.batch_hi}"
+    roofline = roofline_of(st, workload_name, "a profiling pass over one batched step after the timed region")
+
+    # end to end: the instances from pinned host memory, the batched call, and
+    # the results back, every step
+    e2e = None
+    if not args.no_e2e and total_keys:
+        hk = torch.from_numpy(flat.view(np.int32)).pin_memory()
+        hv = iota.cpu().pin_memory()
+        ok_h = torch.empty_like(hk).pin_memory()
+        ov_h = torch.empty_like(hv).pin_memory()
+        reps, tot = min(args.steps, 4), 0.0
+        for r in range(-1, reps):  # (the first untimed)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            keys.copy_(hk, non_blocking=True)
+            vals.copy_(hv, non_blocking=True)
+            run_batched()
+            ok_h.copy_(keys, non_blocking=True)
+            ov_h.copy_(vals, non_blocking=True)
+            torch.cuda.synchronize()
+            if r >= 0:
+                tot += time.perf_counter() - t0
+        e2e = {"value": round(world * reps * total_keys / tot / 1e9, 3), "unit": UNIT,
+               "h2d_bytes_per_step": 8 * total_keys, "d2h_bytes_per_step": 8 * total_keys, "steps": reps,
+               "warmup": 1, "buffers": "pinned host; copies to and from device buffers around sq_sort_batch"}
     all_keys = int(sizes.sum())
     gk_b = world * total_keys / (ms_b / 1e3) / 1e9
     gk_s = world * total_keys / (ms_s / 1e3) / 1e9 if ms_s else None
     return {"metric": METRIC, "value": round(gk_b, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_b, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": f"batch_u32_{count}_instances_2^{args.batch_lo}..2^{args.batch_hi}",
-                       "instances": count,
-                       "total_keys": all_keys, "seed": 7, "cutoff": sq.get_cutoff("u32"),
+            "config": {"workload": workload_name, "instances": count,
+                       "total_keys": all_keys, "seed": 7, "cutoff": "tuned table",
+                       "l2": "inputs larger than L2 (2 x 4 bytes x total_keys, restored before every step)",
                        "parallelism": f"instances sharded over {world} rank(s)"},
+            "roofline": roofline, "e2e": e2e,
             "per_instance_launches": ({"value": round(gk_s, 3), "unit": UNIT, "ms_per_step": round(ms_s, 3)}
                                       if ms_s else None),
             "batched_over_per_instance": round(ms_s / ms_b, 2) if ms_s else None,
-            "gpu_launches_per_step": sum(st["launches"].values()) / max(1, args.steps + args.warmup),
-            "rounds_per_step": st["rounds"] / max(1, args.steps + args.warmup), "verified": ok}
+            "gpu_launches": int(round(launches)), "gpu_launches_per_step": launches,
+            "rounds_per_step": st_timed["rounds"] / max(1, args.steps + args.warmup), "clocks": clk,
+            "verified": ok}
+
+
+def cpu_baseline_batch(args, budget_s: float = 20.0):
+    """The CPU oracle, single-threaded, on the batch's first instances (same
+    sizes and keys) until about budget_s seconds of sorting."""
+    import oracle
+    import workloads as W
+
+    sizes = W.batch_sizes(args.batch_count, 7, args.batch_lo, args.batch_hi)
+    done, t, i = 0, 0.0, 0
+    while i < len(sizes) and t < budget_s:
+        k = W.uniform_u32(int(sizes[i]), (7 << 20) + i + 1)
+        t0 = time.perf_counter()
+        oracle.sort(k, W.iota(k.size), seed=7 + i, cutoff=16384)
+        t += time.perf_counter() - t0
+        done += k.size
+        i += 1
+    return {"value": round(done / t / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"the first {i} instances of the batch ({done} keys), cutoff 16384, single thread",
+            "seconds": round(t, 2)}
+
+
+class RingArena:
+    """Request buffers in one page-locked host allocation, handed out in
+    request order and returned in any order (a ring whose tail advances over
+    the returned prefix)."""
+
+    def __init__(self, nbytes: int):
+        import collections
+        import threading
+
+        import torch
+
+        self.size = nbytes
+        self.buf = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+        self.np = self.buf.numpy()
+        self.recs = collections.deque()
+        self.lock = threading.Lock()
+
+    def alloc(self, nbytes: int):
+        with self.lock:
+            if nbytes > self.size:
+                raise ValueError("request larger than the arena")
+            if not self.recs:
+                start = 0
+            else:
+                head, tail = self.recs[-1][1], self.recs[0][0]
+                if self.recs[-1][0] >= tail:  # live bytes [tail, head): free at the end, then the start
+                    if head + nbytes <= self.size:
+                        start = head
+                    elif nbytes <= tail:
+                        start = 0
+                    else:
+                        return None
+                elif head + nbytes <= tail:  # wrapped: live [tail, end) and [0, head), free [head, tail)
+                    start = head
+                else:
+                    return None
+            rec = [start, start + nbytes, False]
+            self.recs.append(rec)
+            return rec
+
+    def free(self, rec):
+        with self.lock:
+            rec[2] = True
+            while self.recs and self.recs[0][2]:
+                self.recs.popleft()
 
 
 def bench_serve(args, sq, dist, rank, world, local):
     """A Poisson stream of sort requests (sizes log-uniform in [2^10, 2^24],
-    key type uniform over uint32 / uint64 / float32, index payload) served
-    under a 16 GiB budget at 80% of the saturation rate measured by a
-    closed-loop run; reports keys/s and p50/p99 submit-to-done latency."""
+    key type uniform over uint32 / uint64 / float32 with the workload
+    generators, index payload) served under a 16 GiB budget at 80% of the
+    saturation rate of a closed-loop run; keys/s, p50/p99 submit-to-done
+    latency, and the same requests through one sq_sort call each.
+
+    Request i holds n_i keys cut at a seeded offset from a 2^25-key draw of
+    its key type's generator (payload: its own index 0..n_i-1).  Its buffers
+    are page-locked host memory (as a serving process keeps them), filled
+    from the draws by a producer thread ahead of the request's arrival and
+    returned once the request is done, so only the requests in flight hold
+    memory."""
+    import threading
+
     import numpy as np
+    import torch
 
     import workloads as W
 
-    import torch
-
     nreq = args.serve_requests
     reqs = W.serve_requests(nreq, 11, rate_per_s=1.0)  # arrival times rescaled below
-    inputs = [(W.keys_for(dt, n, ks), W.iota(n), dt) for (_, n, dt, ks) in reqs]
-    budget = 16 << 30
-    # request buffers in page-locked host memory (as a serving process keeps
-    # them), so that the server's copies run at the host link's rate
+    src_n = 1 << 25
+    srcs = {"u32": torch.from_numpy(W.uniform_u32(src_n, 1101).view(np.int32)),
+            "u64": torch.from_numpy(W.zipf_u64(src_n, 1102).view(np.int64)),
+            "f32": torch.from_numpy(W.normal_f32(src_n, 1103))}
+    iota = torch.arange(1 << 24, dtype=torch.int32)
+    wbytes = {"u32": 4, "u64": 8, "f32": 4}
     tdt = {"u32": torch.int32, "u64": torch.int64, "f32": torch.float32}
-    bufs = [(torch.empty(k.size, dtype=tdt[dt]).pin_memory().numpy().view(k.dtype),
-             torch.empty(v.size, dtype=torch.int32).pin_memory().numpy().view(v.dtype), dt) for k, v, dt in inputs]
-
-    def run(rate):
-        for (k0, v0, _), (k, v, _) in zip(inputs, bufs):
-            k[...] = k0
-            v[...] = v0
-        srv = sq.Server(budget, device=local)
-        lat, tickets = [], []
-        t0 = time.perf_counter()
-        arrivals = [a / rate for (a, _, _, _) in reqs] if rate else [0.0] * nreq
-        pending = {}
-        i = 0
-        while i < nreq or pending:
-            now = time.perf_counter() - t0
-            while i < nreq and arrivals[i] <= now:
-                k, v, dt = bufs[i]
-                pending[srv.submit(k, v, seed=i, dtype=dt)] = i
-                i += 1
-            for t in list(pending):
-                r = srv.poll(t)
-                if r is not None:
-                    if r[0] != 0:
-                        raise RuntimeError(f"request {pending[t]} failed with status {r[0]}")
-                    lat.append(r[1])
-                    del pending[t]
-            if i < nreq and not pending:
-                time.sleep(max(0.0, min(arrivals[i] - (time.perf_counter() - t0), 0.001)))
-            else:
-                time.sleep(0.0002)
-        wall = time.perf_counter() - t0
-        srv.close()
-        return wall, lat, bufs
-
+    npdt = {"u32": np.uint32, "u64": np.uint64, "f32": np.float32}
+    g = np.random.default_rng(1104)
+    offs = [int(g.integers(0, src_n - n + 1)) for (_, n, _, _) in reqs]
     keys_total = sum(n for (_, n, _, _) in reqs)
-    wall_sat, _, _ = run(0.0)  # closed loop: everything submitted at once
+    budget = 16 << 30
+    arena = RingArena(args.serve_arena_gb << 30)
+    verify_every = max(1, nreq // 2000)
+
+    def producer(ready, stop, count):
+        for i in range(count):
+            _, n, dt, _ = reqs[i]
+            kb = (n * wbytes[dt] + 255) & ~255
+            need = kb + ((n * 4 + 255) & ~255)
+            rec = arena.alloc(need)
+            while rec is None:
+                if stop[0]:
+                    return
+                time.sleep(0.0005)
+                rec = arena.alloc(need)
+            if stop[0]:
+                return
+            k = arena.np[rec[0]:rec[0] + n * wbytes[dt]].view(npdt[dt])
+            v = arena.np[rec[0] + kb:rec[0] + kb + n * 4].view(np.uint32)
+            torch.from_numpy(k.view(np.uint8)).view(tdt[dt]).copy_(srcs[dt][offs[i]:offs[i] + n])
+            torch.from_numpy(v.view(np.int32)).copy_(iota[:n])
+            ready.append((i, rec, k, v))
+
+    def start_producer(count):
+        ready, stop = [], [False]
+        th = threading.Thread(target=producer, args=(ready, stop, count), daemon=True)
+        th.start()
+        return ready, stop, th
+
+    def end_producer(stop, th):
+        stop[0] = True
+        th.join()
+        arena.recs.clear()  # (requests filled but not run are dropped)
+
+    def check(i, k, v):
+        _, n, dt, _ = reqs[i]
+        s0 = srcs[dt][offs[i]:offs[i] + n].to(local)
+        kk = torch.from_numpy(k.view(np.int64 if dt == "u64" else np.int32)).to(local)  # key bits
+        vv = torch.from_numpy(v.view(np.int32)).to(local)
+        if dt == "f32":
+            s0 = s0.view(torch.int32)
+        return check_sorted_any(s0, kk, vv, dt)
+
+    def run_served(rate, clocks=None, limit=None):
+        """Closed loop (rate 0: every request submitted as soon as its
+        buffers are filled) or Poisson arrivals at `rate` requests/s."""
+        count = limit or nreq
+        ready, stop, th = start_producer(count)
+        srv = sq.Server(budget, device=local)
+        lat, pending, nready, i_next, ok, nchk = [], {}, 0, 0, True, 0
+        if clocks is not None:
+            clocks.start()
+        t0 = time.perf_counter()
+        try:
+            while i_next < count or pending:
+                now = time.perf_counter() - t0
+                while i_next < count and nready < len(ready) and (not rate or reqs[i_next][0] / rate <= now):
+                    i, rec, k, v = ready[nready]
+                    nready += 1
+                    pending[srv.submit(k, v, seed=i, dtype=reqs[i][2])] = (i, rec, k, v)
+                    i_next += 1
+                for t in list(pending):
+                    r = srv.poll(t)
+                    if r is not None:
+                        i, rec, k, v = pending.pop(t)
+                        if r[0] != 0:
+                            raise RuntimeError(f"request {i} failed with status {r[0]}")
+                        lat.append(r[1])
+                        if i % verify_every == 0:
+                            ok = ok and check(i, k, v)
+                            nchk += 1
+                        arena.free(rec)
+                time.sleep(0.0002)
+            wall = time.perf_counter() - t0
+        finally:
+            srv.close()
+            end_producer(stop, th)
+        clk = clocks.stop() if clocks is not None else None
+        keys = sum(reqs[i][1] for i in range(count))
+        return wall, keys, np.array(lat), ok, nchk, clk
+
+    def run_per_request(limit=None):
+        """The same requests, closed loop, through one synchronous sq_sort
+        call each (host buffers: the call stages them itself)."""
+        count = limit or nreq
+        ready, stop, th = start_producer(count)
+        t0 = time.perf_counter()
+        ok, nchk = True, 0
+        try:
+            for j in range(count):
+                while j >= len(ready):
+                    time.sleep(0.0002)
+                i, rec, k, v = ready[j]
+                sq.sort(k, v, seed=i, dtype=reqs[i][2])
+                if i % verify_every == 0:
+                    ok = ok and check(i, k, v)
+                    nchk += 1
+                arena.free(rec)
+            wall = time.perf_counter() - t0
+        finally:
+            end_producer(stop, th)
+        return wall, sum(reqs[i][1] for i in range(count)), ok, nchk
+
+    # the producer's own rate (host copies into page-locked memory), alone:
+    # every filled request is returned at once
+    probe = min(nreq, 2000)
+    t0 = time.perf_counter()
+    ready, stop, th = start_producer(probe)
+    j = 0
+    while j < probe:
+        if j < len(ready):
+            arena.free(ready[j][1])
+            j += 1
+        else:
+            time.sleep(0.0002)
+    fill_s = time.perf_counter() - t0
+    end_producer(stop, th)
+    fill_keys = sum(reqs[i][1] for i in range(probe))
+
+    warm = min(nreq, 200)
+    run_served(0.0, limit=warm)  # warm-up: engines, pools, graphs
+    wall_sat, kk, _, ok_sat, chk_sat, _ = run_served(0.0)
     sat_rps = nreq / wall_sat
-    wall, lat, bufs = run(0.8 * sat_rps)
-    ok = all(np_sorted_ok(k0, v0, k, v, dt) for (k0, v0, dt), (k, v, _) in zip(inputs[:32], bufs[:32]))
-    lat = np.array(lat)
-    return {"metric": METRIC, "value": round(keys_total / wall / 1e9, 3), "unit": UNIT, "n_gpus": world,
-            "steps": nreq, "warmup": 0, "ms_per_step": round(wall / nreq * 1e3, 3), "higher_is_better": True,
+    clocks = make_clocks(local)
+    wall, kk, lat, ok_run, chk_run, clk = run_served(0.8 * sat_rps, clocks=clocks)
+    per = None
+    if not args.serve_no_single:
+        wall_one, kk1, ok_one, chk_one = run_per_request()
+        per = {"value": round(kk1 / wall_one / 1e9, 3), "unit": UNIT, "seconds": round(wall_one, 2),
+               "verified": ok_one, "verified_requests": chk_one}
+    st = profiled(sq, lambda: run_served(0.0, limit=min(nreq, 3000)))
+    workload = f"serve_{nreq}_poisson_requests_2^10..2^24"
+    roofline = roofline_of(st, workload, "a profiling pass over the first 3000 requests, closed loop")
+    value = keys_total / wall / 1e9
+    sat = keys_total / wall_sat / 1e9
+    h2d = sum(n * (wbytes[dt] + 4) for (_, n, dt, _) in reqs)
+    return {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+            "steps": nreq, "warmup": warm, "ms_per_step": round(wall / nreq * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64/f32", "data": "synthetic",
-            "config": {"workload": f"serve_{nreq}_poisson_requests_2^10..2^24", "requests": nreq,
-                       "mean_keys": keys_total / nreq, "budget_bytes": budget,
-                       "arrival_rate_rps": round(0.8 * sat_rps, 2), "saturation_rps": round(sat_rps, 2),
-                       "request_buffers": "pinned host",
-                       "saturation_keys_per_s": round(keys_total / wall_sat / 1e9, 3)},
+            "config": {"workload": workload, "requests": nreq, "mean_keys": keys_total / nreq,
+                       "budget_bytes": budget, "arrival_rate_rps": round(0.8 * sat_rps, 2),
+                       "saturation_rps": round(sat_rps, 2), "request_buffers": "pinned host ring arena",
+                       "request_keys": "slices of a 2^25-key draw per key type at seeded offsets",
+                       "l2": "inputs larger than L2 (requests stream from host memory)"},
+            "saturation_keys_per_s": round(sat, 3),
+            "per_request_sq_sort": per,
+            "served_over_per_request": round(sat / per["value"], 2) if per else None,
             "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                           "mean": float(lat.mean())},
-            "verified_sample": ok}
+            "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d // nreq,
+                    "d2h_bytes_per_step": h2d // nreq,
+                    "note": "the served rate itself: requests arrive and leave in host memory"},
+            "host_fill_keys_per_s": round(fill_keys / fill_s / 1e9, 3),
+            "roofline": roofline, "gpu_launches": int(sum(st["launches"].values())),
+            "clocks": clk, "verified": bool(ok_sat and ok_run),
+            "verified_requests": {"saturation": chk_sat, "poisson": chk_run, "every": verify_every}}
+
+
+def cpu_baseline_serve(args, budget_s: float = 20.0):
+    """The CPU oracle, single-threaded, on the first requests of the stream
+    (same sizes and key types) until about budget_s seconds of sorting."""
+    import oracle
+    import workloads as W
+
+    reqs = W.serve_requests(args.serve_requests, 11, rate_per_s=1.0)
+    done, t, i = 0, 0.0, 0
+    while i < len(reqs) and t < budget_s:
+        _, n, dt, ks = reqs[i]
+        k = W.keys_for(dt, n, ks)
+        t0 = time.perf_counter()
+        oracle.sort(k, W.iota(n), seed=i, cutoff=16384, dtype=dt)
+        t += time.perf_counter() - t0
+        done += n
+        i += 1
+    return {"value": round(done / t / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"the first {i} requests of the stream ({done} keys), cutoff 16384, single thread",
+            "seconds": round(t, 2)}
 
 
 # ----------------------------------------------------- the reference arm --
@@ -716,7 +1008,9 @@ def main():
     ap.add_argument("--launch-mode", default="auto", choices=["auto", "host", "graph"],
                     help="how recursion rounds are launched (profilers cannot see kernels inside graph loops)")
     ap.add_argument("--dists", default=",".join(DISTS), help="comma-separated subset (profiling runs)")
-    ap.add_argument("--serve-requests", type=int, default=512)
+    ap.add_argument("--serve-requests", type=int, default=100000)
+    ap.add_argument("--serve-arena-gb", type=int, default=8, help="page-locked host memory for requests in flight")
+    ap.add_argument("--serve-no-single", action="store_true", help="skip the one-sq_sort-per-request comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps are required")
