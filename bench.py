@@ -35,7 +35,7 @@ UNIT = "Gkeys/s"
 DISTS = ["uniform", "sorted", "reverse", "distinct16"]
 DIST_SEED = {"uniform": 2, "sorted": 3, "reverse": 4, "distinct16": 5}
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCES = ["sq_kernels.cuh", "sq_sorter.cuh", "sq_types.cuh"]
+KERNEL_SOURCES = ["sq_kernels.cuh", "sq_sorter.cuh", "sq_types.cuh", "sq_radix.cuh"]
 
 
 def kernel_source_hash() -> str:
