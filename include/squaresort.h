@@ -238,6 +238,21 @@ typedef enum { SQ_LAUNCH_HOST = 0, SQ_LAUNCH_GRAPH = 1, SQ_LAUNCH_AUTO = 2 } sq_
 sq_status sq_set_launch_mode(sq_launch_mode mode);
 sq_launch_mode sq_get_launch_mode(void);
 
+/* Which base-case sort a leaf gets (Algorithm 1's simple_sort, which the
+ * paper leaves open: insertion sort, std::sort below a cutoff, Section 4).
+ * Leaves are sorted by size class: class c holds leaves of up to 64 (c = 0),
+ * 512 (1), 2048 (2) and (c - 2) * 8192 elements (c = 3..10).  Bit c of
+ * `mask` set: leaves of class c with 32-bit key ordinals (SQ_U32, SQ_F32)
+ * take the radix base case (a stable LSD radix sort of the key ordinal on
+ * one CTA per 16K elements, checked against the (key, val) order and merge
+ * sorted where it is not); clear: the merge sort.  Only classes 4..10 have a
+ * radix kernel (other bits are ignored), and SQ_U64 always merge sorts
+ * (sq_set_radix_classes returns SQ_ERR_INVALID for it).  The default mask is
+ * every radix class (0x7F0).  Results do not depend on the mask; the
+ * autotuner measures it.  Process-wide; takes effect at the next call. */
+sq_status sq_set_radix_classes(sq_dtype dtype, uint32_t mask);
+uint32_t sq_get_radix_classes(sq_dtype dtype);
+
 /* Per-kernel-family counters accumulated by all calls of this process.
  * Families: 0 leaf sort, 1 plan, 2 pivots, 3 count, 4 prefix scan,
  * 5 bucket starts, 6 SkewTranspose, 7 child expansion, 8 auxiliary. */

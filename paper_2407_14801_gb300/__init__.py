@@ -89,6 +89,8 @@ def _bind(lib):
         "sq_stats_get": (None, [ctypes.POINTER(Stats)]),
         "sq_stats_reset": (None, []),
         "sq_set_profiling": (None, [i32]),
+        "sq_set_radix_classes": (i32, [i32, u32]),
+        "sq_get_radix_classes": (u32, [i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -339,13 +341,26 @@ LAUNCH_MODES = {"host": 0, "graph": 1, "auto": 2}
 
 def set_launch_mode(mode: str):
     """'host' (a host round trip per recursion round), 'graph' (all rounds in
-    one CUDA-graph launch) or 'auto' (graph for batches and the server)."""
+    one CUDA-graph launch) or 'auto' (currently host rounds everywhere)."""
     _check(lib().sq_set_launch_mode(LAUNCH_MODES[mode]))
 
 
 def get_launch_mode() -> str:
     m = int(lib().sq_get_launch_mode())
     return {v: k for k, v in LAUNCH_MODES.items()}[m]
+
+
+RADIX_CLASSES_ALL = 0x7F0
+
+
+def set_radix_classes(dtype: str, mask: int):
+    """Leaf classes (bit c: class c) sorted by the radix base case for a key
+    type; the others are merge sorted.  uint64 keys take no radix classes."""
+    _check(lib().sq_set_radix_classes(DTYPES[dtype], mask))
+
+
+def get_radix_classes(dtype: str) -> int:
+    return int(lib().sq_get_radix_classes(DTYPES[dtype]))
 
 
 def cutoff_for(dtype: str, n: int) -> int:
@@ -365,6 +380,8 @@ def load_tuning(path: str | None = None) -> bool:
         doc = json.load(f)
     for dtype, table in doc.get("cutoff_by_log2n", {}).items():
         set_cutoff_table(dtype, {int(k): int(v) for k, v in table.items()})
+    for dtype, mask in doc.get("radix_classes", {}).items():
+        set_radix_classes(dtype, int(mask))
     return True
 
 

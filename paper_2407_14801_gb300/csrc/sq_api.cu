@@ -260,6 +260,17 @@ sq_status sq_set_launch_mode(sq_launch_mode mode) {
 
 sq_launch_mode sq_get_launch_mode(void) { return (sq_launch_mode)g_launch_mode.load(); }
 
+sq_status sq_set_radix_classes(sq_dtype dtype, uint32_t mask) {
+  g_err[0] = 0;
+  if (!dtype_ok(dtype)) return fail(SQ_ERR_INVALID, "bad dtype %d", (int)dtype);
+  if (dtype == SQ_U64 && (mask & sq::kRadixClassesAll))
+    return fail(SQ_ERR_INVALID, "uint64 keys have no radix base case");
+  sq::engine_set_radix_classes(dtype, mask);
+  return SQ_OK;
+}
+
+uint32_t sq_get_radix_classes(sq_dtype dtype) { return dtype_ok(dtype) ? sq::engine_get_radix_classes(dtype) : 0u; }
+
 sq_status sq_sort_ex(void *keys, uint32_t *vals, uint64_t n, sq_dtype dtype, uint64_t seed, sq_stream_t stream,
                      const sq_sort_opts *opts) {
   g_err[0] = 0;

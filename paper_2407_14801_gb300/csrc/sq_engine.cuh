@@ -20,6 +20,8 @@ struct StatsBox {
   std::mutex mu;
   EngineStats s{};
   std::atomic<int> profiling{0};
+  // per key type (DT_U32, DT_U64, DT_F32): leaf classes sorted by the radix base case
+  std::atomic<uint32_t> radix_classes[3] = {{kRadixClassesAll}, {0u}, {kRadixClassesAll}};
 };
 StatsBox &stats_box();
 
@@ -200,9 +202,11 @@ struct Engine {
     return e;
   }
 
+  static u32 radix_classes() { return kRadix ? stats_box().radix_classes[DT].load() & kRadixClassesAll : 0u; }
+
   static cudaError_t launch_leaf_class(Launcher &L, const Ctx *cp, int cls, u32 count, int nsm) {
     if constexpr (kRadix) {
-      switch (cls) {  // (class c holds (c - 2) * 8192 elements: 16K, 24K, 32K, ... 64K)
+      if ((radix_classes() >> cls) & 1u) switch (cls) {  // (class c holds (c - 2) * 8192 elements: 16K, 24K, 32K, ... 64K)
         case 4: return launch_leaf_radix<512, 32>(L, cp, 4, count, nsm);
         case 5:
         case 6: return launch_leaf_radix_cluster<512, 32, 2>(L, cp, cls, count, nsm);
@@ -413,6 +417,7 @@ struct Engine {
   // instantiated graph serves every run of this key type on this thread.
   struct GraphSlot {
     int dev = -1, nsm = 0;
+    u32 radix = 0;  // the radix classes the captured leaf launches follow
     Ctx *ctx = nullptr;  // device, 2 contexts
     GraphStats *gs = nullptr;
     cudaStream_t cap = nullptr;
@@ -444,8 +449,9 @@ struct Engine {
 
   // Builds (once per thread, device and instance count) the graph of rounds.
   static int graph_prepare(GraphSlot &G, int dev, int nsm, u32 kmax, char *err, size_t errlen) {
-    if (G.exec && G.dev == dev) return 0;
+    if (G.exec && G.dev == dev && G.radix == radix_classes()) return 0;
     G.reset();
+    G.radix = radix_classes();
     SQ_CU(cudaMalloc((void **)&G.ctx, 2 * sizeof(Ctx) + sizeof(GraphStats)));
     G.gs = reinterpret_cast<GraphStats *>(G.ctx + 2);
     SQ_CU(cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking));

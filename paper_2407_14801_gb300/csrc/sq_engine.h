@@ -126,4 +126,8 @@ void engine_stats_get(EngineStats *out);
 void engine_stats_reset();
 void engine_set_profiling(int on);
 
+// Leaf classes sorted by the radix base case, per key type (sq_set_radix_classes).
+void engine_set_radix_classes(int dtype, uint32_t mask);
+uint32_t engine_get_radix_classes(int dtype);
+
 }  // namespace sq

@@ -20,6 +20,9 @@ void engine_stats_reset() {
 
 void engine_set_profiling(int on) { stats_box().profiling.store(on ? 1 : 0); }
 
+void engine_set_radix_classes(int dtype, uint32_t mask) { stats_box().radix_classes[dtype].store(mask & kRadixClassesAll); }
+uint32_t engine_get_radix_classes(int dtype) { return stats_box().radix_classes[dtype].load(); }
+
 uint32_t engine_max_pivots(int dtype) {
   return dtype == DT_U32 ? Engine<DT_U32>::max_pivots()
                          : (dtype == DT_U64 ? Engine<DT_U64>::max_pivots() : Engine<DT_F32>::max_pivots());

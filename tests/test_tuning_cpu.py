@@ -99,3 +99,55 @@ def test_choose_prefers_larger_cutoffs_within_the_tie():
     assert choose({"8192": 2.0, "32768": 1.9, "65536": 2.1}) == 32768
     t = retable({"u32": {"20": {"8192": 1.0, "65536": 1.3}, "24": {"8192": 1.0, "65536": 1.0}}})
     assert t["u32"]["20"] == 8192 and t["u32"]["24"] == 65536 and t["u32"]["0"] == 8192
+
+
+def test_sweep_report_and_level_steps():
+    """The cutoff-experiment report (no GPU): normalised time is
+    ms * 1e6 / (n log2 n); a table row per size; an extra recursion level is
+    read where the round count rises with n."""
+    from paper_2407_14801_gb300 import autotune as at
+
+    assert abs(at.normalised_ns(1.0, 1 << 20) - 1e6 / ((1 << 20) * 20)) < 1e-12
+    doc = {"cutoffs": [64, 65536], "points": {"u32": {
+        "10": {"64": {"ns_per_n_log2n": 1.0, "rounds": 3}, "65536": {"ns_per_n_log2n": 0.5, "rounds": 1}},
+        "12": {"64": {"ns_per_n_log2n": 1.1, "rounds": 3}, "65536": {"ns_per_n_log2n": 0.4, "rounds": 1}},
+        "14": {"64": {"ns_per_n_log2n": 1.3, "rounds": 5}, "65536": {"ns_per_n_log2n": 0.3, "rounds": 1}},
+        "18": {"64": {"ns_per_n_log2n": 1.4, "rounds": 5}, "65536": {"ns_per_n_log2n": 0.6, "rounds": 4}}}}}
+    text = at.report(doc)
+    assert "| 2^14 | 1.3000 (5) | 0.3000 (1) |" in text
+    assert at.level_steps(doc, "u32", 64) == [14]
+    assert at.level_steps(doc, "u32", 65536) == [18]
+
+
+def test_radix_classes_setting(sq):
+    """sq_set_radix_classes / sq_get_radix_classes (no GPU): per key type, only
+    classes 4..10 kept, uint64 refused, and a tuning file applies its masks."""
+    import os
+    import tempfile
+
+    before = {d: sq.get_radix_classes(d) for d in ("u32", "f32")}
+    try:
+        assert sq.get_radix_classes("u64") == 0
+        sq.set_radix_classes("u32", 0x30)
+        assert sq.get_radix_classes("u32") == 0x30 and sq.get_radix_classes("f32") == before["f32"]
+        sq.set_radix_classes("f32", 0xFFFF)
+        assert sq.get_radix_classes("f32") == sq.RADIX_CLASSES_ALL
+        with pytest.raises(sq.SquareSortError):
+            sq.set_radix_classes("u64", 0x10)
+        sq.set_radix_classes("u64", 0)
+        with tempfile.TemporaryDirectory() as d:
+            path = os.path.join(d, "t.json")
+            with open(path, "w") as f:
+                json.dump({"cutoff_by_log2n": {}, "radix_classes": {"u32": 0x70, "f32": 0x7F0}}, f)
+            assert sq.load_tuning(path)
+        assert sq.get_radix_classes("u32") == 0x70
+    finally:
+        for d, m in before.items():
+            sq.set_radix_classes(d, m)
+
+
+def test_radix_choice_and_class_sizes():
+    from paper_2407_14801_gb300 import autotune as at
+
+    assert [at.class_size(c) for c in at.RADIX_CLASSES] == [16384, 24576, 32768, 40960, 49152, 57344, 65536]
+    assert at.choose_radix(1.0, 1.0) and at.choose_radix(1.01, 1.0) and not at.choose_radix(1.1, 1.0)
