@@ -244,11 +244,11 @@ sq_launch_mode sq_get_launch_mode(void);
  * 512 (1), 2048 (2) and (c - 2) * 8192 elements (c = 3..10).  Bit c of
  * `mask` set: leaves of class c with 32-bit key ordinals (SQ_U32, SQ_F32)
  * take the radix base case (a stable LSD radix sort of the key ordinal on
- * one CTA per 16K elements, checked against the (key, val) order and merge
- * sorted where it is not); clear: the merge sort.  Only classes 4..10 have a
+ * one CTA of up to 16K elements, clusters above that, checked against the (key, val) order and merge
+ * sorted where it is not); clear: the merge sort.  Only classes 2..10 have a
  * radix kernel (other bits are ignored), and SQ_U64 always merge sorts
  * (sq_set_radix_classes returns SQ_ERR_INVALID for it).  The default mask is
- * every radix class (0x7F0).  Results do not depend on the mask; the
+ * every radix class (0x7FC); the binding applies the autotuner's masks.  Results do not depend on the mask; the
  * autotuner measures it.  Process-wide; takes effect at the next call. */
 sq_status sq_set_radix_classes(sq_dtype dtype, uint32_t mask);
 uint32_t sq_get_radix_classes(sq_dtype dtype);

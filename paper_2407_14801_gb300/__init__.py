@@ -350,7 +350,7 @@ def get_launch_mode() -> str:
     return {v: k for k, v in LAUNCH_MODES.items()}[m]
 
 
-RADIX_CLASSES_ALL = 0x7F0
+RADIX_CLASSES_ALL = 0x7FC
 
 
 def set_radix_classes(dtype: str, mask: int):

@@ -86,12 +86,12 @@ def time_cutoff(sq, torch, src, vals0, dtype: str, cutoff: int, reps: int) -> fl
     return times[len(times) // 2]
 
 
-RADIX_CLASSES = tuple(range(4, 11))  # leaf classes with a radix kernel (32-bit key ordinals)
+RADIX_CLASSES = tuple(range(2, 11))  # leaf classes with a radix kernel (32-bit key ordinals)
 
 
 def class_size(c: int) -> int:
-    """The largest leaf of size class c (c >= 3: (c - 2) * 8192 elements)."""
-    return (c - 2) * 8192
+    """The largest leaf of size class c: 64, 512, 2048, then (c - 2) * 8192."""
+    return 64 if c == 0 else 512 if c == 1 else 2048 if c == 2 else (c - 2) * 8192
 
 
 def choose_radix(ms_radix: float, ms_merge: float, tie: float = TIE) -> bool:

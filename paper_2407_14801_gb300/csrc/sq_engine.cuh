@@ -206,7 +206,9 @@ struct Engine {
 
   static cudaError_t launch_leaf_class(Launcher &L, const Ctx *cp, int cls, u32 count, int nsm) {
     if constexpr (kRadix) {
-      if ((radix_classes() >> cls) & 1u) switch (cls) {  // (class c holds (c - 2) * 8192 elements: 16K, 24K, 32K, ... 64K)
+      if ((radix_classes() >> cls) & 1u) switch (cls) {  // (class c holds 2K, 8K, then (c - 2) * 8192 elements)
+        case 2: return launch_leaf_radix<128, 16>(L, cp, 2, count, nsm);
+        case 3: return launch_leaf_radix<512, 16>(L, cp, 3, count, nsm);
         case 4: return launch_leaf_radix<512, 32>(L, cp, 4, count, nsm);
         case 5:
         case 6: return launch_leaf_radix_cluster<512, 32, 2>(L, cp, cls, count, nsm);

@@ -465,8 +465,15 @@ __device__ __noinline__ void leaf_merge_fallback(typename S::E *s, int tid) {
 // checked for presorted input as in k_leaf, then sorted by RadixLeaf (or
 // merge sorted when the radix order is not the (key, val) order).  Leaves
 // of 32-bit key ordinals only (uint32, float32 one-word elements).
+// CTAs per SM a radix leaf kernel is built for: one for the 16K class (its
+// 32 elements a thread need the registers), else the merge kernels' budget.
 template <int DT, int T, int R>
-__global__ void __launch_bounds__(T, 1) k_leaf_radix(const Ctx *__restrict__ cp, int cls, u32 count) {
+constexpr int kRadixMinBlocks() {
+  return T * R >= 16384 ? 1 : kLeafMinBlocks<DT, T, false>();
+}
+
+template <int DT, int T, int R>
+__global__ void __launch_bounds__(T, (kRadixMinBlocks<DT, T, R>())) k_leaf_radix(const Ctx *__restrict__ cp, int cls, u32 count) {
   const Ctx &c = *cp;
   typedef KT<DT> K;
   typedef Sorter<K, T, R, false> S;

@@ -26,7 +26,7 @@ enum : u32 {
 constexpr u32 kNone = 0xffffffffu;
 constexpr int kMaxAttempts = 256;  // pivot samples per node before giving up
 constexpr int kLeafClasses = 11;
-constexpr uint32_t kRadixClassesAll = 0x7F0u;  // leaf classes 4..10 (8K..64K elements) have radix kernels
+constexpr uint32_t kRadixClassesAll = 0x7FCu;  // leaf classes 2..10 (512..64K elements) have radix kernels
 
 // Child kinds (Algorithm 1): the root, a column sort, a bucket sort.
 enum : u32 { KIND_ROOT = 0, KIND_COL = 1, KIND_BUC = 2 };

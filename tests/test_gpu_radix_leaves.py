@@ -1,4 +1,4 @@
-"""GPU parity of the radix base case (leaves of 8K..64K uint32 / float32
+"""GPU parity of the radix base case (leaves of 513..64K uint32 / float32
 keys, one CTA or a cluster of 2-4 CTAs) against the plain definition of
 the result: the input ordered by (ordinal(key), val).
 
@@ -19,7 +19,8 @@ import workloads as W
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-SIZES = [8193, 12000, 16384, 16385, 24576, 24577, 32768, 40000, 49152, 49153, 65535, 65536]
+SIZES = [513, 2048, 2049, 6000, 8192, 8193, 12000, 16384, 16385, 24576, 24577, 32768, 40000, 49152, 49153,
+         65535, 65536]
 
 
 @pytest.fixture(scope="module")
@@ -123,7 +124,7 @@ def test_radix_leaves_in_a_batch_of_mixed_classes(sq):
     """Many leaves of every radix class in the same launches (host-driven
     and persistent grids alike), each equal to its own definition."""
     g = np.random.default_rng(11)
-    sizes = list(g.integers(8193, 65537, size=60)) + SIZES
+    sizes = list(g.integers(513, 65537, size=60)) + SIZES
     items, refs = [], []
     for i, n in enumerate(sizes):
         n = int(n)

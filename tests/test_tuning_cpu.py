@@ -121,7 +121,7 @@ def test_sweep_report_and_level_steps():
 
 def test_radix_classes_setting(sq):
     """sq_set_radix_classes / sq_get_radix_classes (no GPU): per key type, only
-    classes 4..10 kept, uint64 refused, and a tuning file applies its masks."""
+    classes 2..10 kept, uint64 refused, and a tuning file applies its masks."""
     import os
     import tempfile
 
@@ -149,5 +149,5 @@ def test_radix_classes_setting(sq):
 def test_radix_choice_and_class_sizes():
     from paper_2407_14801_gb300 import autotune as at
 
-    assert [at.class_size(c) for c in at.RADIX_CLASSES] == [16384, 24576, 32768, 40960, 49152, 57344, 65536]
+    assert [at.class_size(c) for c in at.RADIX_CLASSES] == [2048, 8192, 16384, 24576, 32768, 40960, 49152, 57344, 65536]
     assert at.choose_radix(1.0, 1.0) and at.choose_radix(1.01, 1.0) and not at.choose_radix(1.1, 1.0)
