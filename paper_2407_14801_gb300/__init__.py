@@ -70,6 +70,7 @@ def _bind(lib):
     sig = {
         "sq_sort": (i32, [vp, vp, u64, i32, u64, vp]),
         "sq_sort_ex": (i32, [vp, vp, u64, i32, u64, vp, ctypes.POINTER(SortOpts)]),
+        "sq_sync": (i32, [vp]),
         "sq_skew_transpose": (i32, [ctypes.POINTER(SkewBuf), u64, u64, vp]),
         "sq_skew_transpose_noalloc": (i32, [ctypes.POINTER(SkewBuf), u64, u64, vp]),
         "sq_sort_batch": (i32, [ctypes.POINTER(SortDesc), u32, vp]),
@@ -176,6 +177,15 @@ def sq_sort(keys, vals=None, seed: int = 0, dtype: str | None = None, cutoff: in
 
 
 sort = sq_sort
+
+
+def sq_sync(stream=None):
+    """Waits for the stream (default: torch's current stream) and raises the
+    first error latched by an asynchronous sort on it (graph launch mode)."""
+    _check(lib().sq_sync(_stream(stream)))
+
+
+sync = sq_sync
 
 
 def sq_skew_transpose(keys_in, vals_in, rows: int, cols: int, pivot_keys, pivot_vals, k: int, keys_out, vals_out,

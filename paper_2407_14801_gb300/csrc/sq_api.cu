@@ -163,6 +163,7 @@ sq_status sort_device(void *keys, uint32_t *vals, uint64_t n, sq_dtype dtype, ui
   spec.ninst = 1;
   spec.cutoff = cutoff;
   spec.graph = graph_for(false);
+  spec.async = !(opts && opts->trace && opts->trace_cap);  // (with graph rounds only)
   std::vector<sq::TraceOut> tr;
   if (opts && opts->trace && opts->trace_cap) {
     tr.resize(opts->trace_cap);
@@ -283,8 +284,13 @@ sq_status sq_sort_ex(void *keys, uint32_t *vals, uint64_t n, sq_dtype dtype, uin
     return fail(SQ_ERR_INVALID, "cutoff %u outside [2, %u]", opts->cutoff, sq::engine_max_leaf(dtype));
   if (opts && opts->trace_cap && !opts->trace) return fail(SQ_ERR_INVALID, "trace_cap without trace buffer");
   if (opts && opts->trace_count) *opts->trace_count = 0;
-  if (n == 0) return SQ_OK;
   cudaStream_t st = (cudaStream_t)stream;
+  {  // an error latched by an earlier asynchronous call on this stream comes first
+    char perr[200] = {0};
+    const int prc = sq::engine_poll(st, perr, sizeof(perr));
+    if (prc) return fail((sq_status)prc, "%s", perr);
+  }
+  if (n == 0) return SQ_OK;
   const size_t w = key_bytes(dtype);
   const bool hk = is_host_ptr(keys), hv = vals && is_host_ptr(vals);
   if (!hk && !hv) return sort_device(keys, vals, n, dtype, seed, st, opts);
@@ -336,6 +342,14 @@ sq_status sq_sort_ex(void *keys, uint32_t *vals, uint64_t n, sq_dtype dtype, uin
   return SQ_OK;
 }
 
+sq_status sq_sync(sq_stream_t stream) {
+  g_err[0] = 0;
+  char err[200] = {0};
+  const int rc = sq::engine_sync((cudaStream_t)stream, err, sizeof(err));
+  if (rc) return fail((sq_status)rc, "%s", err);
+  return SQ_OK;
+}
+
 sq_status sq_sort(void *keys, uint32_t *vals, uint64_t n, sq_dtype dtype, uint64_t seed, sq_stream_t stream) {
   return sq_sort_ex(keys, vals, n, dtype, seed, stream, nullptr);
 }
@@ -379,6 +393,11 @@ sq_status sq_sort_batch(const sq_sort_desc *descs, uint32_t count, sq_stream_t s
   g_err[0] = 0;
   if (count && !descs) return fail(SQ_ERR_INVALID, "descs is NULL");
   cudaStream_t st = (cudaStream_t)stream;
+  {  // an error latched by an earlier asynchronous call on this stream comes first
+    char perr[200] = {0};
+    const int prc = sq::engine_poll(st, perr, sizeof(perr));
+    if (prc) return fail((sq_status)prc, "%s", perr);
+  }
   for (uint32_t i = 0; i < count; i++) {
     if (!dtype_ok(descs[i].dtype)) return fail(SQ_ERR_INVALID, "desc %u: bad dtype", i);
     if (descs[i].n > sq_max_n(descs[i].dtype)) return fail(SQ_ERR_INVALID, "desc %u: n too large", i);
@@ -441,6 +460,7 @@ sq_status sq_sort_batch(const sq_sort_desc *descs, uint32_t count, sq_stream_t s
     spec.ninst = (uint32_t)is.size();
     spec.cutoff = default_cutoff((sq_dtype)d);
     spec.graph = graph_for(true);
+    spec.async = 1;  // (with graph rounds only)
     char err[400] = {0};
     const int rc = run_engine((sq_dtype)d, spec, st, err, sizeof(err));
     if (rc) return fail((sq_status)rc, "batch: %s", err);

@@ -25,6 +25,19 @@ struct StatsBox {
 };
 StatsBox &stats_box();
 
+// An asynchronous run's record: where its status and graph counters land
+// (page-locked), the event after them, and what its statistics need.
+struct PendingRun {
+  Status status;
+  GraphStats gs;
+};
+// Takes a free record for a run on stream st (waiting for the oldest one
+// when all are taken); nullptr if none can be had.  The caller enqueues the
+// copies into it, then calls pending_commit.
+PendingRun *pending_take(cudaStream_t st, double key_bytes, const EngineStats &per_round, uint32_t ninst,
+                         char *err, size_t errlen, int *rc);
+int pending_commit(PendingRun *r, cudaStream_t st, char *err, size_t errlen);
+
 #define SQ_CU(call)                                                                   \
   do {                                                                                \
     cudaError_t e_ = (call);                                                          \
@@ -420,6 +433,7 @@ struct Engine {
   struct GraphSlot {
     int dev = -1, nsm = 0;
     u32 radix = 0;  // the radix classes the captured leaf launches follow
+    cudaStream_t last = nullptr;  // stream of the last launch (its context buffer is this slot's)
     Ctx *ctx = nullptr;  // device, 2 contexts
     GraphStats *gs = nullptr;
     cudaStream_t cap = nullptr;
@@ -647,6 +661,19 @@ struct Engine {
     for (int cl = 0; cl < kLeafClasses; cl++) leaf_cap[cl] = P.leaf_cap[cl];
     const u64 ready_cap = P.ready_cap, fresh_cap = P.fresh_cap, meta_cap = P.meta_cap;
     u64 node_cap = P.node_cap;
+    // An asynchronous run cannot stop for the host to grow the node pool, so
+    // it starts with room for 4 * total_n / cutoff + 4096 recursing nodes
+    // (measured peak, over sizes 2^10..2^28 and cutoffs 64..65536: under
+    // 2 * n / cutoff), and runs synchronously when that pool would be large.
+    bool async = spec.async && spec.graph && !spec.skew_only && !spec.trace_cap &&
+                 stats_box().profiling.load() == 0;
+    if (async) {
+      const u64 want = 4 * (total_n / cutoff) + 4096 + 2 * fresh_cap + ninst;
+      if (want * sizeof(Node) > (1ull << 30) || want > 0xffffffffull)
+        async = false;
+      else
+        node_cap = std::max(node_cap, want);
+    }
     const size_t off = P.slab_bytes, o_inst = P.o_inst, o_ready[2] = {P.o_ready[0], P.o_ready[1]};
     const size_t o_fresh[2] = {P.o_fresh[0], P.o_fresh[1]}, o_cnt = P.o_cnt, o_status = P.o_status;
     const size_t o_meta = P.o_meta, o_done = P.o_done, o_trace = P.o_trace, o_wbase = P.o_wbase;
@@ -892,6 +919,24 @@ struct Engine {
       void *pinned = nullptr;
       SQ_CU(pinned_readback(&pinned));
       Back &hb = *reinterpret_cast<Back *>(pinned);
+      if (G.last && G.last != st) SQ_CU(cudaStreamSynchronize(G.last));  // (its launch reads G.ctx)
+      G.last = st;
+      if (async) {
+        // enqueue the whole recursion, then the copies of its status into a
+        // pending record; the scratch is freed in stream order behind them
+        EngineStats per_round = G.per_round;
+        PendingRun *pr = pending_take(st, (double)KEY_BYTES, per_round, ninst, err, errlen, &rc);
+        if (!pr) return rc ? rc : 5;
+        const Ctx pair[2] = {hctx[0], hctx[1]};
+        GraphStats zero;
+        memset(&zero, 0, sizeof(zero));
+        SQ_CU(cudaMemcpyAsync(G.ctx, pair, sizeof(pair), cudaMemcpyHostToDevice, st));
+        SQ_CU(cudaMemcpyAsync(G.gs, &zero, sizeof(zero), cudaMemcpyHostToDevice, st));
+        SQ_CU(cudaGraphLaunch(G.exec, st));
+        SQ_CU(cudaMemcpyAsync(&pr->gs, G.gs, sizeof(GraphStats), cudaMemcpyDeviceToHost, st));
+        SQ_CU(cudaMemcpyAsync(&pr->status, c.status, sizeof(Status), cudaMemcpyDeviceToHost, st));
+        return pending_commit(pr, st, err, errlen);
+      }
       for (;;) {
         const int q = (int)(rounds & 1);
         const Ctx pair[2] = {hctx[q], hctx[q ^ 1]};  // the body starts with the list parity of round `rounds`

@@ -78,7 +78,18 @@ struct RunSpec {
   // 1: run all rounds as one CUDA-graph launch (device-side loop) instead
   // of one host round trip per round; ignored while profiling.
   int graph;
+  // 1 (with graph, no trace): return once the work is enqueued; the run's
+  // status is collected later by engine_sync / engine_poll on the stream.
+  int async;
 };
+
+// Asynchronous runs still in flight (or finished but not yet collected).
+// engine_sync waits for the stream and collects its runs; engine_poll
+// collects the stream's runs that have finished, without waiting.  Both
+// return 0 or the first run's status code (sq_status values), with its
+// message in err.
+int engine_sync(cudaStream_t st, char *err, size_t errlen);
+int engine_poll(cudaStream_t st, char *err, size_t errlen);
 
 // Device scratch bytes (slab + node record) of a stand-alone SkewTranspose.
 uint64_t engine_skew_scratch_bytes(int dtype, uint64_t n, uint64_t cols, uint64_t k);

@@ -88,8 +88,9 @@ def test_graph_reports_attempts_exhausted_and_recovers(sq):
     sq.set_launch_mode("graph")
     keys = torch.full((100,), 7, dtype=torch.int32, device="cuda")
     vals = torch.zeros(100, dtype=torch.int32, device="cuda")
-    with pytest.raises(sq.SquareSortError) as e:
+    with pytest.raises(sq.SquareSortError) as e:  # from the call, or from sq_sync (asynchronous sort)
         sq.sort(keys, vals, seed=1, dtype="u32", cutoff=16)
+        sq.sync()
     assert e.value.status == 7
     k = W.uniform_u32(5000, 4)
     gk, gv, _, _ = run(sq, "graph", k, W.iota(5000), "u32", 1, 16)
