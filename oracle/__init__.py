@@ -82,6 +82,12 @@ def _bind(lib):
     lib.sqo_isqrt_ceil.argtypes = [u64]
     lib.sqo_sort.restype = i32
     lib.sqo_sort.argtypes = [i32, vp, vp, u64, u64, u64, i32, vp, u64, ctypes.POINTER(u64), vp, vp]
+    if hasattr(lib, "sqo_sort_appendix"):
+        lib.sqo_sort_appendix.restype = i32
+        lib.sqo_sort_appendix.argtypes = [i32, vp, vp, u64, u64, u64, vp, u64, ctypes.POINTER(u64), vp, vp]
+    if hasattr(lib, "sqo_isqrt_floor"):
+        lib.sqo_isqrt_floor.restype = u64
+        lib.sqo_isqrt_floor.argtypes = [u64]
     lib.sqo_skew_transpose.restype = i32
     lib.sqo_skew_transpose.argtypes = [i32, vp, vp, u64, u64, u64, vp, vp, u64, vp, vp, vp, i32]
     lib.sqo_node_buckets.restype = u32
@@ -143,15 +149,22 @@ def isqrt_ceil(n: int, lib=None) -> int:
     return int((lib or load()).sqo_isqrt_ceil(n))
 
 
+def isqrt_floor(n: int, lib=None) -> int:
+    return int((lib or load()).sqo_isqrt_floor(n))
+
+
 # -------------------------------------------------------------- the method --
 
 def sort(keys, vals=None, seed: int = 0, cutoff: int = 16, skew_mode: int = 0, dtype: str = "u32",
-         trace_cap: int = 0, root_skew: bool = False, lib=None):
+         trace_cap: int = 0, root_skew: bool = False, lib=None, variant: str = "algorithm1"):
     """SquareSort (Algorithm 1) of (keys, vals) by (ordinal(key), val).
 
     Returns ``(keys, vals, trace, root_skew)``: sorted copies, the list of
     per-node records (empty unless ``trace_cap``), and the root's array right
     after its SkewTranspose as ``(keys, vals)`` (or None).
+    ``variant="appendix"``: the paper's Appendix listing instead (integer keys;
+    floor(sqrt n) columns with a long last one, pivots sampled from the input,
+    "<=" buckets; ``skew_mode`` is Algorithm 3 there).
     """
     lib = lib or load()
     kb = _key_bits(keys, dtype).copy()
@@ -161,9 +174,16 @@ def sort(keys, vals=None, seed: int = 0, cutoff: int = 16, skew_mode: int = 0, d
     cnt = ctypes.c_uint64(0)
     rk = np.empty_like(kb) if root_skew else None
     rv = np.empty(n, dtype=np.uint32) if root_skew else None
-    st = lib.sqo_sort(DTYPES[dtype], _ptr(kb), _ptr(vv), n, seed & (2**64 - 1), cutoff, skew_mode,
-                      ctypes.cast(trace, ctypes.c_void_p) if trace_cap else None, trace_cap,
-                      ctypes.byref(cnt), _ptr(rk), _ptr(rv))
+    if variant == "appendix":
+        st = lib.sqo_sort_appendix(DTYPES[dtype], _ptr(kb), _ptr(vv), n, seed & (2**64 - 1), cutoff,
+                                   ctypes.cast(trace, ctypes.c_void_p) if trace_cap else None, trace_cap,
+                                   ctypes.byref(cnt), _ptr(rk), _ptr(rv))
+    elif variant == "algorithm1":
+        st = lib.sqo_sort(DTYPES[dtype], _ptr(kb), _ptr(vv), n, seed & (2**64 - 1), cutoff, skew_mode,
+                          ctypes.cast(trace, ctypes.c_void_p) if trace_cap else None, trace_cap,
+                          ctypes.byref(cnt), _ptr(rk), _ptr(rv))
+    else:
+        raise ValueError(variant)
     if st != OK:
         raise RuntimeError(f"oracle sort failed with status {st}")
     recs = [dict(off=r.off, n=r.n, m=r.m, hash=r.hash, depth=r.depth, kind=r.kind, index=r.index,

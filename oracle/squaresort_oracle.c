@@ -35,6 +35,22 @@
  *     node's path (defined below), so that every node's pivots are a pure
  *     function of (seed, path, attempt); the paper leaves the RNG open.
  *
+ * The appendix variant (the paper's Appendix listing, which Section 2.1 says
+ * "deviates slightly" from Algorithm 1), selected by sqo_sort_appendix, for
+ * integer keys as in the listing:
+ *   - m = floor(sqrt(n)) columns of m elements, the last one extended to n;
+ *   - m pivot samples drawn with replacement from the node's input A before
+ *     the column sorts (draws r = 0..m-1 of attempt 0), sorted; the largest
+ *     becomes +inf (a flag); left to right, a sample equal to the next one is
+ *     replaced by its predecessor in the (key, val) order (the listing's
+ *     decrement; the minimum element, which has none, stays);
+ *   - bucket i = { e : pivots[i-1] < e <= pivots[i] } (the listing's "<=");
+ *   - a bucket whose upper pivot is the successor of its lower one holds only
+ *     elements equal to that pivot and is copied instead of sorted;
+ *   - no redraws: one sample per node;
+ *   - the cutoff is at least 3 (with 3 a node of 3 elements would have a
+ *     single column as large as itself).
+ *
  * Random source (Steele, Lea & Flood 2014, "Fast splittable pseudorandom
  * number generators"; output function as in Vigna's splitmix64):
  *   F(z)           = z ^= z>>30; z *= 0xbf58476d1ce4e5b9; z ^= z>>27;
@@ -87,6 +103,7 @@ typedef struct {
   uint64_t trace_cap;
   uint64_t trace_count;
   elem *root_skew; /* optional copy of the root's array right after its SkewTranspose */
+  int variant;     /* 0: Algorithm 1; 1: the appendix listing's variant */
 } ctx;
 
 /* ---------------------------------------------------------------- order --- */
@@ -181,6 +198,12 @@ uint64_t sqo_isqrt_ceil(uint64_t n) {
   return hi;
 }
 
+/* Largest m with m*m <= n. */
+uint64_t sqo_isqrt_floor(uint64_t n) {
+  uint64_t m = sqo_isqrt_ceil(n);
+  return (m * m > n) ? m - 1 : m;
+}
+
 /* --------------------------------------------------------- SkewTranspose --- */
 
 /* Pivot list of a node: pivots[0..m-2] are sampled elements; index m-1 is the
@@ -192,6 +215,7 @@ typedef struct {
 
 static int below_pivot(const ctx *c, const elem *e, const pivots_t *pv, uint64_t idx) {
   if (idx == pv->m - 1) return 1; /* everything is below +inf */
+  if (c->variant) return !elem_less(c->dtype, &pv->p[idx], e); /* appendix: bucket i holds e <= pivot i */
   return elem_less(c->dtype, e, &pv->p[idx]);
 }
 
@@ -352,6 +376,90 @@ out:
   free(piv);
 }
 
+/* ------------------------------------------------- the appendix variant --- */
+
+/* The element just below e in the (key, val) order of integer keys (e itself
+ * for the minimum element, which has no predecessor). */
+static elem elem_pred(elem e) {
+  if (e.val > 0) {
+    e.val--;
+  } else if (e.key > 0) {
+    e.key--;
+    e.val = 0xffffffffu;
+  }
+  return e;
+}
+
+/* The appendix listing's pivot step, on the node's input A before its column
+ * sorts: m samples with replacement, sorted; index m-1 becomes the +inf flag;
+ * equal neighbours separated by replacing the lower one by its predecessor. */
+static void appendix_pivots(const ctx *c, const elem *A, uint64_t n, uint64_t m, uint64_t h, elem *smp) {
+  for (uint64_t r = 0; r < m; r++) smp[r] = A[sqo_scale(sqo_pivot_draw(h, 0, r), n)];
+  library_sort(c->dtype, smp, m);
+  for (uint64_t r = 0; r + 2 < m; r++) /* (index m-1 is +inf now: never equal) */
+    if (elem_equal(c->dtype, &smp[r], &smp[r + 1])) smp[r] = elem_pred(smp[r]);
+}
+
+/* SquareSort as the appendix listing states it: A[0..n) sorted into D[0..n). */
+static void square_sort_appendix(ctx *c, elem *A, elem *D, uint64_t n, uint64_t off, uint64_t h,
+                                 uint32_t depth, uint32_t kind, uint32_t index) {
+  if (c->status != SQO_OK) return;
+  if (n <= c->cutoff) { /* the base case: a library sort */
+    memcpy(D, A, (size_t)n * sizeof(elem));
+    library_sort(c->dtype, D, n);
+    return;
+  }
+  const uint64_t m = sqo_isqrt_floor(n);
+  uint64_t *first = malloc(m * sizeof(uint64_t)), *last = malloc(m * sizeof(uint64_t));
+  uint64_t *starts = malloc((m + 1) * sizeof(uint64_t)), *cnt = malloc(m * sizeof(uint64_t));
+  uint64_t *slot = malloc(m * sizeof(uint64_t));
+  elem *smp = malloc(m * sizeof(elem));
+  if (!first || !last || !starts || !cnt || !slot || !smp) {
+    c->status = SQO_ERR_NOMEM;
+    goto done;
+  }
+  /* pivots from the input, before any column is sorted */
+  appendix_pivots(c, A, n, m, h, smp);
+  /* m columns of m elements; the last one runs to n */
+  for (uint64_t i = 0; i < m; i++) {
+    first[i] = i * m;
+    last[i] = (i + 1 < m) ? (i + 1) * m : n;
+  }
+  for (uint64_t i = 0; i < m; i++)
+    square_sort_appendix(c, A + first[i], D + first[i], last[i] - first[i], off + first[i],
+                         sqo_child_hash(h, 1, i), depth + 1, 1, (uint32_t)i);
+  if (c->status != SQO_OK) goto done;
+  record(c, off, n, m, h, depth, kind, index, 1);
+  pivots_t pv = {smp, m};
+  bucket_sizes(c, D, m, first, last, &pv, cnt);
+  starts[0] = 0;
+  for (uint64_t b = 0; b < m; b++) starts[b + 1] = starts[b] + cnt[b];
+  for (uint64_t b = 0; b < m; b++) slot[b] = starts[b];
+  run_skew(c, D, A, m, first, last, m, &pv, slot);
+  if (depth == 0 && c->root_skew) memcpy(c->root_skew, A, (size_t)n * sizeof(elem));
+  for (uint64_t b = 0; b < m; b++) {
+    const uint64_t len = starts[b + 1] - starts[b];
+    elem lowp;
+    int mono = 0; /* upper pivot the successor of the lower one: only copies of it */
+    if (b > 0 && b + 1 < m) {
+      lowp = elem_pred(smp[b]);
+      mono = elem_less(c->dtype, &smp[b - 1], &smp[b]) && elem_equal(c->dtype, &lowp, &smp[b - 1]);
+    }
+    if (mono)
+      memcpy(D + starts[b], A + starts[b], (size_t)len * sizeof(elem));
+    else if (len)
+      square_sort_appendix(c, A + starts[b], D + starts[b], len, off + starts[b],
+                           sqo_child_hash(h, 2, b), depth + 1, 2, (uint32_t)b);
+  }
+done:
+  free(first);
+  free(last);
+  free(starts);
+  free(cnt);
+  free(slot);
+  free(smp);
+}
+
 /* ---------------------------------------------------------- entry points --- */
 
 static void load_elems(int dtype, const void *keys, const uint32_t *vals, uint64_t n, elem *e) {
@@ -392,9 +500,44 @@ int sqo_sort(int dtype, void *keys, uint32_t *vals, uint64_t n, uint64_t seed, u
     return SQO_ERR_NOMEM;
   }
   load_elems(dtype, keys, vals, n, A);
-  ctx c = {dtype, cutoff, skew_mode, SQO_OK, trace, trace_cap, 0, rs};
+  ctx c = {dtype, cutoff, skew_mode, SQO_OK, trace, trace_cap, 0, rs, 0};
   if (rs) memcpy(rs, A, (size_t)n * sizeof(elem)); /* a leaf root has no skew: keep input */
   square_sort(&c, A, D, n, 0, sqo_root_hash(seed), 0, 0, 0);
+  if (c.status == SQO_OK) {
+    store_elems(dtype, D, n, keys, vals);
+    if (rs) store_elems(dtype, rs, n, root_skew_keys, root_skew_vals);
+  }
+  if (trace_count) *trace_count = c.trace_count;
+  free(A);
+  free(D);
+  free(rs);
+  return c.status;
+}
+
+/* Sorts (keys, vals) in place with the appendix variant (arguments as
+ * sqo_sort; integer keys only: SQO_U32 or SQO_U64). */
+int sqo_sort_appendix(int dtype, void *keys, uint32_t *vals, uint64_t n, uint64_t seed, uint64_t cutoff,
+                      sqo_node *trace, uint64_t trace_cap, uint64_t *trace_count, void *root_skew_keys,
+                      uint32_t *root_skew_vals) {
+  /* cutoff >= 3: a node has n >= 4, so m = floor(sqrt n) >= 2 and every column and bucket is smaller than the node */
+  if ((dtype != SQO_U32 && dtype != SQO_U64) || cutoff < 3) return SQO_ERR_INVALID;
+  if (n > 0xffffffffull) return SQO_ERR_INVALID;
+  if (n == 0) {
+    if (trace_count) *trace_count = 0;
+    return SQO_OK;
+  }
+  elem *A = malloc((size_t)n * sizeof(elem)), *D = malloc((size_t)n * sizeof(elem));
+  elem *rs = root_skew_keys ? malloc((size_t)n * sizeof(elem)) : NULL;
+  if (!A || !D || (root_skew_keys && !rs)) {
+    free(A);
+    free(D);
+    free(rs);
+    return SQO_ERR_NOMEM;
+  }
+  load_elems(dtype, keys, vals, n, A);
+  ctx c = {dtype, cutoff, 0, SQO_OK, trace, trace_cap, 0, rs, 1};
+  if (rs) memcpy(rs, A, (size_t)n * sizeof(elem));
+  square_sort_appendix(&c, A, D, n, 0, sqo_root_hash(seed), 0, 0, 0);
   if (c.status == SQO_OK) {
     store_elems(dtype, D, n, keys, vals);
     if (rs) store_elems(dtype, rs, n, root_skew_keys, root_skew_vals);
@@ -432,7 +575,7 @@ int sqo_skew_transpose(int dtype, const void *keys_in, const uint32_t *vals_in, 
     col[i] = (i * rows < n) ? i * rows : n;
     colEnd[i] = ((i + 1) * rows < n) ? (i + 1) * rows : n;
   }
-  ctx c = {dtype, 2, mode, SQO_OK, NULL, 0, 0, NULL};
+  ctx c = {dtype, 2, mode, SQO_OK, NULL, 0, 0, NULL, 0};
   pivots_t pv = {piv, k};
   bucket_sizes(&c, A, cols, col, colEnd, &pv, size);
   bucket_start[0] = 0;
@@ -471,7 +614,7 @@ uint32_t sqo_node_buckets(const uint64_t *keys, uint64_t n, uint64_t h, uint64_t
     colEnd[i] = ((i + 1) * m < n) ? (i + 1) * m : n;
     if (colEnd[i] > col[i]) library_sort(SQO_U64, D + col[i], colEnd[i] - col[i]);
   }
-  ctx c = {SQO_U64, 2, 0, SQO_OK, NULL, 0, 0, NULL};
+  ctx c = {SQO_U64, 2, 0, SQO_OK, NULL, 0, 0, NULL, 0};
   attempts = select_pivots(&c, D, n, m, col, colEnd, h, piv);
   if (attempts) {
     pivots_t pv = {piv, m};
