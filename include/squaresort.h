@@ -79,7 +79,7 @@ sq_status sq_sort(void *keys, uint32_t *vals, uint64_t n, sq_dtype dtype, uint64
 typedef struct {
   uint64_t off;      /* first element of the node in the array */
   uint64_t n;        /* node size */
-  uint64_t m;        /* ceil(sqrt(n)): columns = buckets */
+  uint64_t m;        /* columns = buckets: ceil(sqrt(n)) (floor under SQ_APPENDIX) */
   uint64_t hash;     /* path hash that seeds its pivot draws */
   uint32_t depth;    /* root = 0 */
   uint32_t kind;     /* 0 root, 1 column child, 2 bucket child */
@@ -87,11 +87,23 @@ typedef struct {
   uint32_t index;    /* column / bucket index within the parent */
 } sq_trace_rec;
 
+/* Recursion variants.  SQ_ALGORITHM1 is Algorithm 1 (Section 2.1).
+ * SQ_APPENDIX is the code the paper prints in its appendix, which Section 2.1
+ * says departs slightly from Algorithm 1: m = floor(sqrt n) columns of m
+ * elements, the last one extended to the end of the node; m pivot samples
+ * drawn once (no redraws) from the node's input before its columns are
+ * sorted, the largest replaced by +inf and each sample equal to the next one
+ * lowered to its predecessor in the (key, val) order; bucket i holds the
+ * elements e with p_{i-1} < e <= p_i.  Integer keys only (SQ_U32, SQ_U64),
+ * a cutoff of at least 3, and n < sq_max_n(dtype). */
+typedef enum { SQ_ALGORITHM1 = 0, SQ_APPENDIX = 1 } sq_variant;
+
 typedef struct {
   uint32_t cutoff;        /* leaf iff n <= cutoff; 0 = the default; 2..sq_max_leaf(dtype) */
   uint32_t trace_cap;     /* capacity of `trace` in records (0 = no trace) */
   sq_trace_rec *trace;    /* host array receiving node records (any order) */
   uint32_t *trace_count;  /* out: records produced (may exceed trace_cap) */
+  uint32_t variant;       /* sq_variant; 0 = Algorithm 1 */
 } sq_sort_opts;
 
 /* sq_sort with an explicit leaf cutoff and an optional recursion trace.

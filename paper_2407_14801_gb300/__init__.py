@@ -38,7 +38,12 @@ class TraceRec(ctypes.Structure):
 
 class SortOpts(ctypes.Structure):
     _fields_ = [("cutoff", ctypes.c_uint32), ("trace_cap", ctypes.c_uint32),
-                ("trace", ctypes.POINTER(TraceRec)), ("trace_count", ctypes.POINTER(ctypes.c_uint32))]
+                ("trace", ctypes.POINTER(TraceRec)), ("trace_count", ctypes.POINTER(ctypes.c_uint32)),
+                ("variant", ctypes.c_uint32)]
+
+
+# sq_variant: Algorithm 1, or the variant the paper prints in its appendix
+VARIANTS = {"algorithm1": 0, "appendix": 1}
 
 
 class SkewBuf(ctypes.Structure):
@@ -153,20 +158,23 @@ def _stream(stream):
 # ----------------------------------------------------------------- sq_sort --
 
 def sq_sort(keys, vals=None, seed: int = 0, dtype: str | None = None, cutoff: int = 0, stream=None,
-            trace_cap: int = 0):
+            trace_cap: int = 0, variant: str = "algorithm1"):
     """Sort (keys, vals) in place (CUDA tensors, or CPU tensors / numpy arrays,
     which the library stages through device memory).  Returns the list of
-    per-node trace records when ``trace_cap`` > 0, else None."""
+    per-node trace records when ``trace_cap`` > 0, else None.  ``variant``:
+    "algorithm1" or "appendix" (integer keys, cutoff >= 3)."""
     n = _numel(keys)
     if vals is not None and _numel(vals) != n:
         raise ValueError("keys and vals differ in length")
+    if variant not in VARIANTS:
+        raise ValueError(f"variant {variant!r}: one of {sorted(VARIANTS)}")
     opts = None
     recs = None
     cnt = ctypes.c_uint32(0)
-    if cutoff or trace_cap:
+    if cutoff or trace_cap or VARIANTS[variant]:
         recs = (TraceRec * max(trace_cap, 1))()
         opts = SortOpts(cutoff, trace_cap, ctypes.cast(recs, ctypes.POINTER(TraceRec)) if trace_cap else None,
-                        ctypes.pointer(cnt))
+                        ctypes.pointer(cnt), VARIANTS[variant])
     st = lib().sq_sort_ex(_ptr(keys), _ptr(vals), n, _dtype_of(keys, dtype), seed & (2**64 - 1), _stream(stream),
                           ctypes.byref(opts) if opts is not None else None)
     _check(st)

@@ -157,6 +157,7 @@ sq_status sort_device(void *keys, uint32_t *vals, uint64_t n, sq_dtype dtype, ui
   }
   is.n = n;
   is.seed = seed;
+  is.variant = opts ? opts->variant : 0;
   sq::RunSpec spec;
   memset(&spec, 0, sizeof(spec));
   spec.inst = &is;
@@ -283,6 +284,15 @@ sq_status sq_sort_ex(void *keys, uint32_t *vals, uint64_t n, sq_dtype dtype, uin
   if (opts && opts->cutoff && (opts->cutoff < 2 || opts->cutoff > sq::engine_max_leaf(dtype)))
     return fail(SQ_ERR_INVALID, "cutoff %u outside [2, %u]", opts->cutoff, sq::engine_max_leaf(dtype));
   if (opts && opts->trace_cap && !opts->trace) return fail(SQ_ERR_INVALID, "trace_cap without trace buffer");
+  if (opts && opts->variant > SQ_APPENDIX) return fail(SQ_ERR_INVALID, "unknown variant %u", opts->variant);
+  if (opts && opts->variant == SQ_APPENDIX) {
+    if (dtype == SQ_F32) return fail(SQ_ERR_INVALID, "the appendix variant sorts integer keys");
+    if (opts->cutoff == 2 || (!opts->cutoff && cutoff_for(dtype, n) < 3))
+      return fail(SQ_ERR_INVALID, "the appendix variant needs a cutoff of at least 3");
+    if (n >= sq_max_n(dtype))
+      return fail(SQ_ERR_INVALID, "n = %llu: the appendix variant takes n < %llu", (unsigned long long)n,
+                  (unsigned long long)sq_max_n(dtype));
+  }
   if (opts && opts->trace_count) *opts->trace_count = 0;
   cudaStream_t st = (cudaStream_t)stream;
   {  // an error latched by an earlier asynchronous call on this stream comes first

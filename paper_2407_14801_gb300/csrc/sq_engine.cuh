@@ -278,7 +278,7 @@ struct Engine {
 
   static cudaError_t launch_all_pivots(Launcher &L, const Ctx *cp, u32 ready, u32 max_k, int nsm) {
     cudaError_t e = cudaSuccess;
-    const u32 maxp = max_k ? max_k - 1 : 0;
+    const u32 maxp = max_k;  // (an appendix-variant node sorts k samples, one more than its pivots)
     e = launch_pivots<32, 16, true>(L, cp, ready, 0, 512, nsm);
     if (e == cudaSuccess && maxp > 512) e = launch_pivots<128, 16, false>(L, cp, ready, 512, 2048, nsm);
     if (e == cudaSuccess && maxp > 2048) e = launch_pivots<512, 16, false>(L, cp, ready, 2048, 8192, nsm);
@@ -656,6 +656,13 @@ struct Engine {
                (unsigned long long)max_n, (unsigned long long)lim);
       return 1;
     }
+    for (u32 i = 0; i < ninst && !spec.skew_only; i++)
+      if (spec.inst[i].variant &&
+          (spec.inst[i].n >= lim || cutoff_of(i) < 3 || (DT != DT_U32 && DT != DT_U64))) {
+        snprintf(err, errlen, "the appendix variant takes integer keys, n < %llu and a cutoff >= 3",
+                 (unsigned long long)lim);
+        return 1;
+      }
     const Plan P = make_plan(total_n, ninst, cutoff, cutoff_max, spec.trace_cap, spec.skew_only, (u32)spec.k, (u32)spec.cols);
     u32 leaf_cap[kLeafClasses];
     for (int cl = 0; cl < kLeafClasses; cl++) leaf_cap[cl] = P.leaf_cap[cl];
@@ -682,6 +689,7 @@ struct Engine {
       for (int cl = 0; cl < kLeafClasses; cl++) o_leaves[q][cl] = P.o_leaves[q][cl];
     char *slab = nullptr;
     Node *nodes = nullptr;
+    u32 *samp = nullptr;
     auto dalloc = [&](void **p, size_t bytes) -> cudaError_t {
       if (spec.dev_alloc) {
         *p = spec.dev_alloc(spec.alloc_ctx, bytes);
@@ -694,6 +702,7 @@ struct Engine {
       cudaStream_t st;
       char **slab;
       Node **nodes;
+      u32 **samp;
       void rel(void *p) {
         if (!p) return;
         if (spec.dev_free)
@@ -704,10 +713,34 @@ struct Engine {
       ~Free() {
         rel(*slab);
         rel(*nodes);
+        rel(*samp);
       }
-    } free_guard{spec, st, &slab, &nodes};
+    } free_guard{spec, st, &slab, &nodes, &samp};
     SQ_CU(dalloc((void **)&slab, off));
     SQ_CU(dalloc((void **)&nodes, sizeof(Node) * node_cap));
+    // Appendix variant: the store for the pivot samples of nodes whose
+    // columns recurse (drawn at expansion, read at the pivot step).  Such a
+    // node keeps floor(sqrt n) samples, at most 3n/cutoff (its m or its last
+    // column, at most 3m+1 elements, exceeds the cutoff), and the nodes of one
+    // depth are disjoint; min(8, 24/cutoff) * n covers the totals measured
+    // over cutoffs 3..64 (3.9 n at cutoff 3) with room to spare.  A run that
+    // needs more stops with the sample-store error.
+    u64 samp_cap = 0;
+    {
+      u64 var_n = 0;
+      u32 var_cut = 0xffffffffu;
+      for (u32 i = 0; i < ninst; i++)
+        if (spec.inst[i].variant) {
+          var_n += spec.inst[i].n;
+          var_cut = std::min(var_cut, cutoff_of(i));
+        }
+      if (var_n) {
+        const double per = std::min(8.0, 24.0 / (double)var_cut);
+        const u64 elems = (u64)(per * (double)var_n) + 4 * (u64)std::sqrt((double)var_n) + 4096;
+        samp_cap = elems * (K::key_words + 1) + 2;
+        SQ_CU(dalloc((void **)&samp, 4 * samp_cap));
+      }
+    }
 
     Ctx c;
     memset(&c, 0, sizeof(c));
@@ -721,6 +754,8 @@ struct Engine {
     c.fix_cap = (u32)std::min<u64>(P.fix_cap, 0xffffffffull);
     c.runs = (RunCopy *)(slab + P.o_runs);
     c.runs_cap = (u32)P.runs_cap;
+    c.samp = samp;
+    c.samp_cap = samp_cap;
     c.fresh_cap = (u32)fresh_cap;
     c.status = (Status *)(slab + o_status);
     c.meta = (u32 *)(slab + o_meta);
@@ -772,7 +807,7 @@ struct Engine {
       hinst[i].tags = is.tags;
       hinst[i].n = is.n;
       hinst[i].cutoff = cutoff_of(i);
-      hinst[i].pad = 0;
+      hinst[i].variant = is.variant;
       if (spec.skew_only) continue;
       if (is.n == 0) {
         hs.done++;
@@ -792,9 +827,10 @@ struct Engine {
       } else {
         Node nd;
         memset(&nd, 0, sizeof(nd));
-        const u32 m = isqrt_ceil(is.n);
+        const u32 m = node_m(is.n, is.variant);
         nd.off = 0;
         nd.hash = root_hash(is.seed);
+        nd.samp = kNoSamp;
         nd.n = (u32)is.n;
         nd.rows = nd.cols = nd.k = m;
         nd.inst = i;
@@ -803,16 +839,17 @@ struct Engine {
         nd.out = 0;
         nd.src = 1;
         const u32 id = (u32)hnodes.size();
-        if (m <= hinst[i].cutoff && m >= kHostExpandCols) {
+        const u32 ncol = std::min<u32>(m, (u32)((is.n + m - 1) / m));  // non-empty columns
+        const u64 last = is.n - (u64)(ncol - 1) * m;                     // the last one runs to n
+        if (std::max<u64>(m, last) <= hinst[i].cutoff && m >= kHostExpandCols) {
           // a large root whose columns are leaves: spawn them here rather than
           // in one CTA of k_expand_cols
-          const u32 ncol = (u32)((is.n + m - 1) / m);
           nd.pending = (int)ncol;
           for (u32 q = 0; q < ncol; q++) {
             const u64 st0 = (u64)q * m;
             Leaf L;
             L.off = st0;
-            L.n = (u32)std::min<u64>(m, is.n - st0);
+            L.n = (u32)(q + 1 == ncol ? last : (u64)m);
             L.inst = i;
             L.parent = id;
             L.flags = KIND_COL | (1u << 8) | LEAF_SRC;  // the root's columns: from the source into D
@@ -834,6 +871,7 @@ struct Engine {
       nd.cols = (u32)spec.cols;
       nd.k = (u32)spec.k;
       nd.parent = kNone;
+      nd.samp = kNoSamp;
       hnodes.push_back(nd);
       hc[0].ready = 1;
       hc[0].max_ready_k = nd.k;
@@ -896,7 +934,7 @@ struct Engine {
     };
     auto status_error = [&](const Status &S) -> int {
       if (!(S.error & ~ERRB_TRACE)) return 0;
-      snprintf(err, errlen, "engine error bits 0x%x (1 pivot attempts, 2 nodes, 4 list, 8 arena, 16 sizes)",
+      snprintf(err, errlen, "engine error bits 0x%x (1 pivot attempts, 2 nodes, 4 list, 8 arena, 16 sizes, 64 sample store)",
                S.error);
       return (S.error & ERRB_ATTEMPTS) ? 7 : ((S.error & ERRB_SIZES) ? 8 : 2);
     };
@@ -1164,7 +1202,7 @@ struct Engine {
     // The instance in `slot` (free: its previous occupant completed) starts in
     // the next round.  The caller keeps the elements in flight within the plan.
     int admit(const InstSpec &is, u32 slot, char *err, size_t errlen) {
-      if (slot >= sp.ninst_cap || is.n == 0 || !is.tags) {
+      if (slot >= sp.ninst_cap || is.n == 0 || !is.tags || is.variant) {
         snprintf(err, errlen, "bad admission (slot %u, n %llu)", slot, (unsigned long long)is.n);
         return 1;
       }
@@ -1188,6 +1226,7 @@ struct Engine {
       hi.tags = is.tags;
       hi.n = is.n;
       hi.cutoff = cut;
+      hi.variant = is.variant;
       const int q = (int)(round & 1);  // the next round's lists
       std::vector<Leaf> add[kLeafClasses];
       auto put_leaf = [&](const Leaf &L) {
@@ -1208,9 +1247,10 @@ struct Engine {
       } else {
         if (int rc = grow_nodes((u64)nodes_used + 1 + P.fresh_cap, err, errlen)) return rc;
         memset(&nd, 0, sizeof(nd));
-        const u32 m = isqrt_ceil(is.n);
+        const u32 m = node_m(is.n, is.variant);
         nd.off = 0;
         nd.hash = root_hash(is.seed);
+        nd.samp = kNoSamp;
         nd.n = (u32)is.n;
         nd.rows = nd.cols = nd.k = m;
         nd.inst = slot;
@@ -1220,13 +1260,14 @@ struct Engine {
         nd.src = 1;
         has_node = true;
         const u32 id = nodes_used;
-        if (m <= cut && m >= kHostExpandCols) {  // its columns are leaves: spawn them here
-          const u32 ncol = (u32)((is.n + m - 1) / m);
+        const u32 ncol = std::min<u32>(m, (u32)((is.n + m - 1) / m));  // non-empty columns
+        const u64 last = is.n - (u64)(ncol - 1) * m;                     // the last one runs to n
+        if (std::max<u64>(m, last) <= cut && m >= kHostExpandCols) {     // its columns are leaves: spawn them here
           nd.pending = (int)ncol;
           for (u32 i = 0; i < ncol; i++) {
             Leaf L;
             L.off = (u64)i * m;
-            L.n = (u32)std::min<u64>(m, is.n - L.off);
+            L.n = (u32)(i + 1 == ncol ? last : (u64)m);
             L.inst = slot;
             L.parent = id;
             L.flags = KIND_COL | (1u << 8) | LEAF_SRC;
@@ -1307,7 +1348,7 @@ struct Engine {
         G.sorts += S.done - done_seen;
       }
       if (S.error & ~ERRB_TRACE) {
-        snprintf(err, errlen, "engine error bits 0x%x (1 pivot attempts, 2 nodes, 4 list, 8 arena, 16 sizes)",
+        snprintf(err, errlen, "engine error bits 0x%x (1 pivot attempts, 2 nodes, 4 list, 8 arena, 16 sizes, 64 sample store)",
                  S.error);
         return (S.error & ERRB_ATTEMPTS) ? 7 : ((S.error & ERRB_SIZES) ? 8 : 2);
       }

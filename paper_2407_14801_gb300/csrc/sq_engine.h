@@ -46,6 +46,7 @@ struct InstSpec {
   uint64_t n;
   uint64_t seed;
   uint32_t cutoff;  // 0: RunSpec::cutoff
+  uint32_t variant; // 0: Algorithm 1; 1: the appendix listing's variant (integer keys, cutoff >= 3)
 };
 
 struct TraceOut {

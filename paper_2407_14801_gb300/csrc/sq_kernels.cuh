@@ -60,13 +60,20 @@ __host__ __device__ __forceinline__ int class_of(u32 n, int nclass) {
   return c < nclass ? c : nclass - 1;
 }
 
-// number of pivots <= e in piv[lo, hi)
+// e lies below pivot p: e < p under Algorithm 1 (bucket j = [p_j, p_{j+1})),
+// e <= p under the appendix variant (bucket i = (p_{i-1}, p_i]).
+template <class K>
+__device__ __forceinline__ bool below_p(const typename K::elem_t &e, const typename K::elem_t &p, bool le) {
+  return le ? !K::lt(p, e) : K::lt(e, p);
+}
+
+// number of pivots in piv[lo, hi) that e is not below (its bucket, from lo)
 template <class K>
 __device__ __forceinline__ int upper_bound_e(const typename K::elem_t *piv, int lo, int hi,
-                                             const typename K::elem_t &e) {
+                                             const typename K::elem_t &e, bool le = false) {
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
-    if (K::lt(e, piv[mid]))
+    if (below_p<K>(e, piv[mid], le))
       hi = mid;
     else
       lo = mid + 1;
@@ -82,16 +89,16 @@ __device__ __forceinline__ int upper_bound_e(const typename K::elem_t *piv, int 
 // input, at most 32.)
 template <class K, int kSpan = 4>
 __device__ __forceinline__ int warp_bucket_from(const typename K::elem_t *piv, int lo, int np,
-                                                const typename K::elem_t &e) {
+                                                const typename K::elem_t &e, bool lep = false) {
   static_assert(kSpan >= 2 && kSpan <= 32, "probe spacing");
   const int lane = threadIdx.x & 31;
   int idx = lo + (lane + 1) * kSpan - 1;  // probes lo+3, lo+7, ...
-  bool le = idx < np && !K::lt(e, piv[idx]);
+  bool le = idx < np && !below_p<K>(e, piv[idx], lep);
   u32 m = __ballot_sync(0xffffffffu, le);
-  if (m == 0xffffffffu) return upper_bound_e<K>(piv, lo + 32 * kSpan, np, e);
-  const int base = lo + __popc(m) * kSpan;  // all pivots below base are <= e
+  if (m == 0xffffffffu) return upper_bound_e<K>(piv, lo + 32 * kSpan, np, e, lep);
+  const int base = lo + __popc(m) * kSpan;  // e is not below any pivot before base
   idx = base + (lane < kSpan - 1 ? lane : kSpan - 1);
-  le = lane < kSpan - 1 && idx < np && !K::lt(e, piv[idx]);
+  le = lane < kSpan - 1 && idx < np && !below_p<K>(e, piv[idx], lep);
   m = __ballot_sync(0xffffffffu, le);
   return base + __popc(m);
 }
@@ -909,12 +916,113 @@ static __global__ void __launch_bounds__(1024) k_plan(const Ctx *__restrict__ cp
 // D with replacement, sort the drawn elements, and redraw the whole sample if
 // two are equal or the smallest is min(D) (the smallest column head).
 
+// The element just below e in the (key, val) order of integer keys (e itself
+// for the minimum).  Float keys never take the appendix variant.
+template <class K>
+__device__ __forceinline__ typename K::elem_t pred_elem(typename K::elem_t e) {
+  if constexpr (K::key_words == 2) {  // uint64 keys: (key, val)
+    if (e.x) {
+      --e.x;
+    } else if (e.k) {
+      --e.k;
+      e.x = 0xffffffffu;
+    }
+    return e;
+  } else if constexpr (sizeof(typename K::elem_t) == 8 && !K::lossy) {  // uint32 keys: key << 32 | val
+    return e ? e - 1 : e;
+  } else {
+    return e;
+  }
+}
+
+// Records a node's accepted pivot sample in the trace.
+__device__ __forceinline__ void trace_node(const Ctx &c, const Node *nd, u32 attempts) {
+  if (!c.trace) return;
+  const u32 ti = atomicAdd(&c.status->trace_used, 1u);
+  if (ti < c.trace_cap) {
+    TraceRec tr;
+    tr.off = nd->off;
+    tr.n = nd->n;
+    tr.m = nd->k;
+    tr.hash = nd->hash;
+    tr.depth = nd->depth;
+    tr.kind = nd->kind;
+    tr.attempts = attempts;
+    tr.index = nd->index;
+    c.trace[ti] = tr;
+  } else {
+    atomicOr(&c.status->error, ERRB_TRACE);
+  }
+}
+
+// The pivot step of the paper's appendix listing: k (= m) samples drawn with
+// replacement from the node's input A (which the column sorts, writing D,
+// leave as it was), sorted; the largest becomes +inf (k-1 pivots remain);
+// a sample equal to the one after it is replaced by its predecessor (each
+// comparison with the sample as drawn: the listing lowers only the earlier
+// one of a pair).  One sample, no redraws.
+template <class K, class S, int T, int R, bool WARP>
+__device__ __forceinline__ void pivots_appendix(const Ctx &c, Node *nd, typename K::elem_t *s, int tid) {
+  typedef typename K::elem_t E;
+  typedef typename K::key_t key_t;
+  const u32 ns = nd->k;  // samples
+  const Inst I = c.inst[nd->inst];
+  const key_t *ak = (const key_t *)(nd->src ? I.skeys : I.keys) + nd->off;
+  const u32 *av = (nd->src ? I.svals : I.vals) + nd->off;
+  const u64 n = nd->n;
+  const u64 sa = attempt_seed(nd->hash, 0);
+  const bool stored = nd->samp != kNoSamp;  // drawn when the node was expanded (see sample_appendix)
+  const key_t *sk = stored ? reinterpret_cast<const key_t *>(c.samp + nd->samp) : nullptr;
+  const u32 *sv = stored ? c.samp + nd->samp + (u64)ns * K::key_words : nullptr;
+  E x[R];
+#pragma unroll
+  for (int q = 0; q < R; q++) {
+    const u32 r = tid * R + q;
+    if (r < ns) {
+      if (stored) {
+        x[q] = K::make(sk[r], sv[r]);
+      } else {
+        const u64 t = __umul64hi(draw(sa, r), n);
+        x[q] = K::make(ak[t], av[t]);
+      }
+    } else {
+      x[q] = K::top();
+    }
+  }
+  S::sort(x, s, tid);
+  s[tid] = x[0];
+  S::sync();
+  const E after = s[tid + 1];  // the next thread's first sample (read before anyone rewrites s)
+  const MetaLayout ML = meta_layout(nd->k, nd->cols, nd->ncb, nd->nkb, K::key_words);
+  key_t *pk = reinterpret_cast<key_t *>(c.meta + nd->meta + ML.pk);
+  u32 *pv = c.meta + nd->meta + ML.pv;
+#pragma unroll
+  for (int q = 0; q < R; q++) {
+    const u32 r = tid * R + q;
+    if (r + 1 < ns) {  // (sample ns-1 is the +inf flag)
+      E e = x[q];
+      if (r + 2 < ns && K::eq(e, q + 1 < R ? x[q + 1] : after)) e = pred_elem<K>(e);
+      pk[r] = K::key(e);
+      pv[r] = K::val(e);
+    }
+  }
+  if (tid == 0) {
+    nd->attempts = 1;
+    trace_node(c, nd, 1);
+  }
+  S::sync();  // the group is done with s before it takes the next node
+}
+
 template <class K, class S, int T, int R, bool WARP>
 __device__ __forceinline__ void pivots_node(const Ctx &c, Node *nd, typename K::elem_t *s, int tid) {
   typedef typename K::elem_t E;
   typedef typename K::key_t key_t;
   const u32 np = nd->k - 1;  // pivots to draw
   const Inst I = c.inst[nd->inst];
+  if (I.variant == VAR_APPENDIX) {
+    pivots_appendix<K, S, T, R, WARP>(c, nd, s, tid);
+    return;
+  }
   const key_t *dk = (const key_t *)I.dkeys + nd->off;
   const u32 *dv = I.dvals + nd->off;
   const u64 n = nd->n;
@@ -1027,8 +1135,10 @@ __global__ void __launch_bounds__(WARP ? 256 : T) k_pivots(const Ctx *__restrict
   for (u32 ri = blockIdx.x * groups + g; ri < ready_count; ri += gridDim.x * groups) {
     const u32 id = c.ready_cur[ri];
     Node *nd = &c.nodes[id];
-    const u32 np = nd->k - 1;  // pivots to draw
-    if (np <= pmin || np > pmax) continue;
+    // elements this group sorts: the k-1 drawn pivots, or the appendix
+    // variant's k samples
+    const u32 need = c.inst[nd->inst].variant == VAR_APPENDIX ? nd->k : nd->k - 1;
+    if (need <= pmin || need > pmax) continue;
     if (nd->meta + meta_layout(nd->k, nd->cols, nd->ncb, nd->nkb, K::key_words).total > c.meta_cap) continue;
     pivots_node<K, S, T, R, WARP>(c, nd, smem + g * S::SMEM, tid);
   }
@@ -1086,11 +1196,12 @@ __global__ void __launch_bounds__(1024) k_count(const Ctx *__restrict__ cp, u32 
     uint8_t *tg = I.tags ? I.tags + nd.off : nullptr;
     u32 *P = meta + ML.P;
     const u32 rows = nd.rows, n = nd.n, cols = nd.cols, nkb = nd.nkb;
+    const bool le = I.variant == VAR_APPENDIX;  // buckets bounded above by "<="
     const u32 Iblk = u - nd.unit_base;
     const u32 i0 = Iblk * kCountCols;
     const u32 i1 = min(cols, i0 + kCountCols);
-    const u32 q0 = (u32)min((u64)i0 * rows, (u64)n);
-    const u32 q1 = (u32)min((u64)i1 * rows, (u64)n);
+    const u32 q0 = (u32)col_begin(i0, rows, n);
+    const u32 q1 = i1 >= cols ? n : (u32)col_begin(i1, rows, n);
     const u32 S = q1 - q0;
     constexpr int CR = kCountR;  // consecutive elements a lane, kCountR * 32 a warp group
     const u32 per_warp = (((S + NW - 1) / NW) + 32 * CR - 1) / (32 * CR) * (32 * CR);
@@ -1098,7 +1209,7 @@ __global__ void __launch_bounds__(1024) k_count(const Ctx *__restrict__ cp, u32 
     const u32 we = q0 + min(S, warp * per_warp + per_warp);
     // column ci and offset pos of this lane's first element, advanced 32*CR per group
     const u32 p_l = ws + (u32)(CR * lane);
-    u32 ci = p_l / rows, pos = p_l - ci * rows;
+    u32 ci = min(p_l / rows, cols - 1), pos = p_l - ci * rows;  // (the last column runs to n)
     int carry_b = -1;
     u32 carry_i = kNone;
     for (u32 gs = ws; gs < we; gs += 32 * CR) {
@@ -1114,7 +1225,7 @@ __global__ void __launch_bounds__(1024) k_count(const Ctx *__restrict__ cp, u32 
         u32 c2 = ci, p2 = pos;
 #pragma unroll
         for (int r = 0; r < CR; r++) {
-          while (p2 >= rows) {
+          while (p2 >= rows && c2 + 1 < cols) {
             p2 -= rows;
             ++c2;
           }
@@ -1137,19 +1248,19 @@ __global__ void __launch_bounds__(1024) k_count(const Ctx *__restrict__ cp, u32 
       if (i_first == i_last) {  // one column: buckets ascend through the group
         const int lo = i_first == carry_i ? carry_b : 0;
         const E elast = shfl_e(my_last_e, llast);
-        const int hi = warp_bucket_from<K, 4 * CR>(piv, lo, np, elast);
-        bk[0] = upper_bound_e<K>(piv, lo, hi, ev[0]);
+        const int hi = warp_bucket_from<K, 4 * CR>(piv, lo, np, elast, le);
+        bk[0] = upper_bound_e<K>(piv, lo, hi, ev[0], le);
 #pragma unroll
         for (int r = 1; r < CR; r++) {  // gallop from the previous element's bucket
           int lo2 = bk[r - 1], st = 1, b = hi;
           for (;;) {
             const int idx = lo2 + st - 1;
             if (idx >= hi) {
-              b = upper_bound_e<K>(piv, lo2, hi, ev[r]);
+              b = upper_bound_e<K>(piv, lo2, hi, ev[r], le);
               break;
             }
-            if (K::lt(ev[r], piv[idx])) {
-              b = upper_bound_e<K>(piv, lo2, idx, ev[r]);
+            if (below_p<K>(ev[r], piv[idx], le)) {
+              b = upper_bound_e<K>(piv, lo2, idx, ev[r], le);
               break;
             }
             lo2 = idx + 1;
@@ -1159,7 +1270,7 @@ __global__ void __launch_bounds__(1024) k_count(const Ctx *__restrict__ cp, u32 
         }
       } else {
 #pragma unroll
-        for (int r = 0; r < CR; r++) bk[r] = upper_bound_e<K>(piv, 0, np, ev[r]);
+        for (int r = 0; r < CR; r++) bk[r] = upper_bound_e<K>(piv, 0, np, ev[r], le);
       }
       // the bucket before the lane's first element (in its column; -1 at a column start)
       int bprev = __shfl_up_sync(0xffffffffu, bk[CR - 1], 1);
@@ -1168,7 +1279,7 @@ __global__ void __launch_bounds__(1024) k_count(const Ctx *__restrict__ cp, u32 
           bprev = carry_b;
         } else if (pr[0] != 0 && pl < we) {  // first element of this warp's range, mid-column
           const E pe = K::make(dk[pl - 1], dv[pl - 1]);
-          bprev = upper_bound_e<K>(piv, 0, np, pe);
+          bprev = upper_bound_e<K>(piv, 0, np, pe, le);
         }
       }
       int lastb = bk[0];
@@ -1206,7 +1317,7 @@ __global__ void __launch_bounds__(1024) k_count(const Ctx *__restrict__ cp, u32 
         const int bp = q == 0 ? -1 : (r > 0 ? bk[r - 1] : bprev);
         const u32 jb1 = (u32)b / kSkewBkts;
         for (u32 Jb = (u32)(bp + kSkewBkts) / kSkewBkts; Jb <= jb1; ++Jb) P[(u64)Jb * cols + c2] = q;
-        const u32 len = min(rows, n - c2 * rows);  // (c2 * rows <= q's position < n)
+        const u32 len = (u32)(col_end(c2, rows, cols, n) - c2 * rows);  // (c2 * rows <= q's position < n)
         if (q + 1 == len)
           for (u32 Jb = jb1 + 1; Jb < nkb; ++Jb) P[(u64)Jb * cols + c2] = len;
       }
@@ -1214,7 +1325,7 @@ __global__ void __launch_bounds__(1024) k_count(const Ctx *__restrict__ cp, u32 
       carry_b = __shfl_sync(0xffffffffu, lastb, llast);
       carry_i = i_last;
       pos += 32 * CR;
-      while (pos >= rows) {
+      while (pos >= rows && ci + 1 < cols) {
         pos -= rows;
         ++ci;
       }
@@ -1368,7 +1479,7 @@ __global__ void __launch_bounds__(256) k_skew(const Ctx *__restrict__ cp, u32 re
       if ((u32)lane < nc) {
         const u32 i = i0 + lane;
         const u64 cs = (u64)i * nd.rows;
-        const u32 len = cs < nd.n ? (u32)min((u64)nd.rows, nd.n - cs) : 0;
+        const u32 len = cs < nd.n ? (u32)(col_end(i, nd.rows, nd.cols, nd.n) - cs) : 0;
         u32 s0 = 0, s1 = 0;
         if (len) {
           s0 = P[(u64)Jb * nd.cols + i];
@@ -1453,8 +1564,9 @@ __global__ void __launch_bounds__(256) k_skew(const Ctx *__restrict__ cp, u32 re
             }
             const int lo = carry_b < 0 ? 0 : carry_b;
             const E elast = shfl_e(e, lastv);
-            const int hi = warp_bucket_from<K>(sm.piv, lo, npiv, elast);
-            jb = valid ? upper_bound_e<K>(sm.piv, lo, hi, e) : hi;
+            const bool le = c.inst[nd.inst].variant == VAR_APPENDIX;
+            const int hi = warp_bucket_from<K>(sm.piv, lo, npiv, elast, le);
+            jb = valid ? upper_bound_e<K>(sm.piv, lo, hi, e, le) : hi;
           }
           const int prevb = __shfl_up_sync(0xffffffffu, jb, 1);
           const int nextb = __shfl_down_sync(0xffffffffu, jb, 1);
@@ -1679,7 +1791,7 @@ __global__ void __launch_bounds__(32 * SQ_SKEW_WARPS, 32 / SQ_SKEW_WARPS) k_skew
       if ((u32)lane < nc) {
         const u32 i = i0 + lane;
         const u64 cs = (u64)i * nd.rows;
-        const u32 len = cs < nd.n ? (u32)min((u64)nd.rows, nd.n - cs) : 0;
+        const u32 len = cs < nd.n ? (u32)(col_end(i, nd.rows, nd.cols, nd.n) - cs) : 0;
         u32 s0 = 0, s1 = 0;
         if (len) {
           s0 = P[(u64)Jb * nd.cols + i];
@@ -1898,10 +2010,11 @@ static __device__ void spawn_batch(const Ctx &c, bool has, const Child &ch, u32 
       const u32 fi = fbase + local;
       if (id < c.node_cap && fi < c.fresh_cap) {
         Node nn;
-        const u32 m = isqrt_ceil(ch.n);
+        const u32 m = node_m(ch.n, c.inst[ch.inst].variant);
         nn.off = ch.off;
         nn.hash = ch.hash;
         nn.meta = 0;
+        nn.samp = kNoSamp;
         nn.n = ch.n;
         nn.rows = nn.cols = nn.k = m;
         nn.inst = ch.inst;
@@ -1988,15 +2101,21 @@ __global__ void __launch_bounds__(256) k_expand_buckets(const Ctx *__restrict__ 
     const MetaLayout ML = meta_layout(nd.k, nd.cols, nd.ncb, nd.nkb, KT<DT>::key_words);
     const u32 *b = c.meta + nd.meta + ML.b;
     const u32 chunk = u - c.wbase[3ull * c.ready_cap + s_ri];
-    if (chunk == 0 && threadIdx.x == 0) c.nodes[id].pending = (int)nd.k;
+    // Under the appendix variant a bucket may be empty (a pivot lowered to
+    // its predecessor need not be an element of the node); the node then
+    // waits for its non-empty buckets only, which every chunk adds to its
+    // pending count (zero since its last column finished; its children
+    // start in the next round).
+    const bool var = c.inst[nd.inst].variant == VAR_APPENDIX;
+    if (!var && chunk == 0 && threadIdx.x == 0) c.nodes[id].pending = (int)nd.k;
     const u32 j = chunk * kExpandChunk + threadIdx.x;
     Child ch;
     bool has = false;
     if (threadIdx.x < kExpandChunk && j < nd.k) {
       ch.n = b[j + 1] - b[j];
       has = true;
-      if (ch.n == 0) {  // cannot happen for a valid pivot sample
-        atomicOr(&c.status->error, ERRB_SIZES);
+      if (ch.n == 0) {
+        if (!var) atomicOr(&c.status->error, ERRB_SIZES);  // cannot happen for a valid Algorithm 1 sample
         has = false;
       }
       ch.off = nd.off + b[j];
@@ -2009,7 +2128,50 @@ __global__ void __launch_bounds__(256) k_expand_buckets(const Ctx *__restrict__ 
       ch.out = nd.out;
       ch.src = 0;  // a bucket reads what its parent's SkewTranspose wrote
     }
+    if (var) {
+      const int nonempty = __syncthreads_count(has);
+      if (threadIdx.x == 0 && nonempty) atomicAdd(&c.nodes[id].pending, nonempty);
+    }
     spawn_batch(c, has, ch, c.fresh_cur, &c.cnt_cur->fresh, LeafCfg<DT>::nclass);
+  }
+}
+
+// The appendix variant draws a node's pivot sample from its input before its
+// columns are sorted.  A column that recurses rewrites its part of that
+// input (its own SkewTranspose lands there), so a node with such a column
+// copies its k draws to the sample store here, before its columns start, and
+// its pivot step reads them back; a node whose columns are all leaves draws
+// from its input at the pivot step, which the leaf sorts leave as it was.
+template <int DT>
+__device__ void sample_appendix(const Ctx &c, u32 id, const Node &nd, const Inst &I, u32 ncol) {
+  typedef KT<DT> K;
+  typedef typename K::key_t key_t;
+  __shared__ u64 s_off;
+  const u64 last = (u64)nd.n - (u64)(ncol - 1) * nd.rows;  // the last column runs to n
+  if (max((u64)nd.rows, last) <= I.cutoff) return;         // (the same for the whole block)
+  const u32 k = nd.k;
+  const u64 words = ((u64)k * (K::key_words + 1) + 1) & ~1ull;  // (even: 8-byte keys stay aligned)
+  if (threadIdx.x == 0) {
+    u64 o = atomicAdd(&c.status->samp_used, words);
+    if (o + words > c.samp_cap) {
+      atomicOr(&c.status->error, ERRB_SAMP);
+      o = kNoSamp;
+    }
+    s_off = o;
+    c.nodes[id].samp = o;
+  }
+  __syncthreads();
+  const u64 o = s_off;
+  if (o == kNoSamp) return;
+  const key_t *ak = (const key_t *)(nd.src ? I.skeys : I.keys) + nd.off;
+  const u32 *av = (nd.src ? I.svals : I.vals) + nd.off;
+  const u64 sa = attempt_seed(nd.hash, 0);
+  key_t *sk = reinterpret_cast<key_t *>(c.samp + o);
+  u32 *sv = c.samp + o + (u64)k * K::key_words;
+  for (u32 r = threadIdx.x; r < k; r += blockDim.x) {
+    const u64 t = __umul64hi(draw(sa, r), (u64)nd.n);
+    sk[r] = ak[t];
+    sv[r] = av[t];
   }
 }
 
@@ -2026,15 +2188,17 @@ __global__ void __launch_bounds__(256) k_expand_cols(const Ctx *__restrict__ cp)
     if (u >= min(c.cnt_cur->fresh, c.fresh_cap)) break;
     const u32 id = c.fresh_cur[u];
     const Node nd = c.nodes[id];
-    const u32 ncol = (u32)(((u64)nd.n + nd.rows - 1) / nd.rows);  // non-empty columns
+    const u32 ncol = min(nd.cols, (u32)(((u64)nd.n + nd.rows - 1) / nd.rows));  // non-empty columns
     if (threadIdx.x == 0) c.nodes[id].pending = (int)ncol;
+    const Inst I = c.inst[nd.inst];
+    if (I.variant == VAR_APPENDIX) sample_appendix<DT>(c, id, nd, I, ncol);
     for (u32 base = 0; base < ncol; base += blockDim.x) {
       const u32 i = base + threadIdx.x;
       Child ch;
       const bool has = i < ncol;
       if (has) {
         const u64 st = (u64)i * nd.rows;
-        ch.n = (u32)min((u64)nd.rows, (u64)nd.n - st);
+        ch.n = (u32)(i + 1 == ncol ? (u64)nd.n - st : (u64)nd.rows);  // (the last one runs to n)
         ch.off = nd.off + st;
         ch.hash = col_hash(nd.hash, i);
         ch.inst = nd.inst;

@@ -21,6 +21,7 @@ enum : u32 {
   ERRB_ARENA = 8u,     // per-round metadata arena full
   ERRB_SIZES = 16u,    // bucket sizes do not add up (internal error)
   ERRB_TRACE = 32u,    // trace buffer full (records dropped)
+  ERRB_SAMP = 64u,     // appendix-variant sample store full
 };
 
 constexpr u32 kNone = 0xffffffffu;
@@ -213,6 +214,34 @@ __host__ __device__ __forceinline__ u32 isqrt_ceil(u64 n) {
   return (u32)m;
 }
 
+// Largest m with m*m <= n.
+__host__ __device__ __forceinline__ u32 isqrt_floor(u64 n) {
+  const u32 m = isqrt_ceil(n);
+  return (u64)m * m > n ? m - 1 : m;
+}
+
+// The recursion a sort follows: Algorithm 1, or the variant of the paper's
+// appendix listing (floor(sqrt n) columns, the last one running to n;
+// pivots sampled from the node's input; buckets bounded above by "<=").
+enum : u32 { VAR_ALG1 = 0, VAR_APPENDIX = 1 };
+
+// Columns of a node (geometry rows x cols over n elements): column i spans
+// [col_begin, col_end); the last column runs to n -- short or empty under
+// Algorithm 1 (ceil(sqrt n) columns), the longest under the appendix variant.
+__host__ __device__ __forceinline__ u64 col_begin(u64 i, u32 rows, u64 n) {
+  const u64 b = i * rows;
+  return b < n ? b : n;
+}
+__host__ __device__ __forceinline__ u64 col_end(u64 i, u32 rows, u32 cols, u64 n) {
+  if (i + 1 >= cols) return n;
+  const u64 e = (i + 1) * rows;
+  return e < n ? e : n;
+}
+// m of a new node of n elements.
+__host__ __device__ __forceinline__ u32 node_m(u64 n, u32 variant) {
+  return variant == VAR_APPENDIX ? isqrt_floor(n) : isqrt_ceil(n);
+}
+
 // ------------------------------------------------------- work structures ----
 
 // One sort instance: the caller's buffers (A) and the scratch copy (D).
@@ -227,8 +256,8 @@ struct Inst {
   u32 *fvals;         //   writes directly
   uint8_t *tags;  // per element of D: its bucket within its 64-bucket block (written by the count)
   u64 n;
-  u32 cutoff;  // leaf iff a node's n <= cutoff (per instance)
-  u32 pad;
+  u32 cutoff;   // leaf iff a node's n <= cutoff (per instance)
+  u32 variant;  // VAR_ALG1 or VAR_APPENDIX
 };
 
 // A SquareSort call with n > cutoff (or a stand-alone SkewTranspose).
@@ -238,6 +267,7 @@ struct Node {
   u64 off;   // first element in the instance
   u64 hash;  // path hash
   u64 meta;  // word offset of this round's metadata in the arena
+  u64 samp;  // appendix variant: word offset of the node's pivot sample in the sample store, or kNoSamp
   u32 n, rows, cols, k;
   u32 inst, parent, kind, index;
   u32 depth, out;  // out: 0 = result lands in A, 1 = in D
@@ -247,6 +277,8 @@ struct Node {
   u32 ncb, nkb, ncs;                    // count blocks, bucket blocks, skew column blocks
   u32 src;  // 1: the node's input is the instance's source (the root, and column children of such nodes)
 };
+
+constexpr u64 kNoSamp = ~0ull;  // the sample is read from the node's input at its pivot step
 
 // A leaf: sorted in one group of threads (n <= cutoff).
 struct Leaf {
@@ -275,6 +307,7 @@ struct Status {
   // per-round work totals written by the plan step
   u32 units, tiles, srows, echunks;
   u64 meta_words;
+  u64 samp_used;  // words of the appendix-variant sample store handed out
   // persistent-kernel work cursors (zeroed every round, with fix_count and
   // the leaf cursors of graph-launched rounds)
   u32 cur_count, cur_scan, cur_skew, cur_expand, cur_ebkt, cur_fix, fix_count;
@@ -335,6 +368,8 @@ struct Ctx {
   u32 ninst;                    // instances of the run
   RunCopy *runs;                // run copies the SkewTranspose hands to k_copy_runs
   u32 runs_cap;
+  u32 *samp;                    // appendix variant: pivot samples of nodes whose columns recurse
+  u64 samp_cap;                 // (words)
 };
 
 // Metadata layout of a ready node (32-bit words from Node::meta), each
