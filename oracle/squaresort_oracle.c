@@ -36,20 +36,27 @@
  *     function of (seed, path, attempt); the paper leaves the RNG open.
  *
  * The appendix variant (the paper's Appendix listing, which Section 2.1 says
- * "deviates slightly" from Algorithm 1), selected by sqo_sort_appendix, for
+ * departs a little from Algorithm 1), selected by sqo_sort_appendix, for
  * integer keys as in the listing:
  *   - m = floor(sqrt(n)) columns of m elements, the last one extended to n;
  *   - m pivot samples drawn with replacement from the node's input A before
  *     the column sorts (draws r = 0..m-1 of attempt 0), sorted; the largest
- *     becomes +inf (a flag); left to right, a sample equal to the next one is
- *     replaced by its predecessor in the (key, val) order (the listing's
- *     decrement; the minimum element, which has none, stays);
+ *     is replaced by the greatest pair (the listing's INT_MAX: a value of the
+ *     order like any other, above or equal to every element); left to right,
+ *     a sample equal to the next one is replaced by its predecessor in the
+ *     (key, val) order (the listing's decrement; the least pair (0, 0), which
+ *     has none, stays);
  *   - bucket i = { e : pivots[i-1] < e <= pivots[i] } (the listing's "<=");
- *   - a bucket whose upper pivot is the successor of its lower one holds only
- *     elements equal to that pivot and is copied instead of sorted;
+ *   - a bucket whose range holds a single (key, val) pair holds only copies
+ *     of it and is copied instead of sorted: as in the listing, bucket i > 0
+ *     when pivots[i-1] is the predecessor of pivots[i]; and, because the
+ *     order is bounded below where the listing's int keys are not, bucket 0
+ *     when pivot 0 is the least pair (without it a node made only of copies
+ *     of (0, 0) would recurse on itself forever);
  *   - no redraws: one sample per node;
- *   - the cutoff is at least 3 (with 3 a node of 3 elements would have a
- *     single column as large as itself).
+ *   - the cutoff is at least 8, so that every node has m >= 3 samples (with
+ *     m = 2 the one pivot of a node of equal elements is that element and
+ *     its bucket 0 is the whole node again; the listing's cutoff is 1000).
  *
  * Random source (Steele, Lea & Flood 2014, "Fast splittable pseudorandom
  * number generators"; output function as in Vigna's splitmix64):
@@ -390,13 +397,23 @@ static elem elem_pred(elem e) {
   return e;
 }
 
+/* The greatest (key, val) pair of a key type. */
+static elem elem_top(int dtype) {
+  elem t;
+  t.key = dtype == SQO_U64 ? ~(uint64_t)0 : 0xffffffffu;
+  t.val = 0xffffffffu;
+  return t;
+}
+
 /* The appendix listing's pivot step, on the node's input A before its column
- * sorts: m samples with replacement, sorted; index m-1 becomes the +inf flag;
- * equal neighbours separated by replacing the lower one by its predecessor. */
+ * sorts: m samples with replacement, sorted; index m-1 becomes the greatest
+ * pair; equal neighbours separated by replacing the lower one by its
+ * predecessor. */
 static void appendix_pivots(const ctx *c, const elem *A, uint64_t n, uint64_t m, uint64_t h, elem *smp) {
   for (uint64_t r = 0; r < m; r++) smp[r] = A[sqo_scale(sqo_pivot_draw(h, 0, r), n)];
   library_sort(c->dtype, smp, m);
-  for (uint64_t r = 0; r + 2 < m; r++) /* (index m-1 is +inf now: never equal) */
+  smp[m - 1] = elem_top(c->dtype);
+  for (uint64_t r = 0; r + 1 < m; r++)
     if (elem_equal(c->dtype, &smp[r], &smp[r + 1])) smp[r] = elem_pred(smp[r]);
 }
 
@@ -439,10 +456,12 @@ static void square_sort_appendix(ctx *c, elem *A, elem *D, uint64_t n, uint64_t 
   if (depth == 0 && c->root_skew) memcpy(c->root_skew, A, (size_t)n * sizeof(elem));
   for (uint64_t b = 0; b < m; b++) {
     const uint64_t len = starts[b + 1] - starts[b];
-    elem lowp;
-    int mono = 0; /* upper pivot the successor of the lower one: only copies of it */
-    if (b > 0 && b + 1 < m) {
-      lowp = elem_pred(smp[b]);
+    int mono; /* the bucket's range holds one (key, val) pair: only copies of it */
+    if (b == 0) {
+      const elem least = {0, 0};
+      mono = elem_equal(c->dtype, &smp[0], &least);
+    } else {
+      const elem lowp = elem_pred(smp[b]);
       mono = elem_less(c->dtype, &smp[b - 1], &smp[b]) && elem_equal(c->dtype, &lowp, &smp[b - 1]);
     }
     if (mono)
@@ -519,8 +538,10 @@ int sqo_sort(int dtype, void *keys, uint32_t *vals, uint64_t n, uint64_t seed, u
 int sqo_sort_appendix(int dtype, void *keys, uint32_t *vals, uint64_t n, uint64_t seed, uint64_t cutoff,
                       sqo_node *trace, uint64_t trace_cap, uint64_t *trace_count, void *root_skew_keys,
                       uint32_t *root_skew_vals) {
-  /* cutoff >= 3: a node has n >= 4, so m = floor(sqrt n) >= 2 and every column and bucket is smaller than the node */
-  if ((dtype != SQO_U32 && dtype != SQO_U64) || cutoff < 3) return SQO_ERR_INVALID;
+  /* cutoff >= 8: a node has n >= 9, so m = floor(sqrt n) >= 3; every column is smaller than the node, and so is
+   * every bucket that is not copied (a bucket holding the whole node lies between two pivots that are an
+   * element and its predecessor, or below a pivot equal to the least pair) */
+  if ((dtype != SQO_U32 && dtype != SQO_U64) || cutoff < 8) return SQO_ERR_INVALID;
   if (n > 0xffffffffull) return SQO_ERR_INVALID;
   if (n == 0) {
     if (trace_count) *trace_count = 0;
