@@ -89,13 +89,16 @@ typedef struct {
 
 /* Recursion variants.  SQ_ALGORITHM1 is Algorithm 1 (Section 2.1).
  * SQ_APPENDIX is the code the paper prints in its appendix, which Section 2.1
- * says departs slightly from Algorithm 1: m = floor(sqrt n) columns of m
+ * says departs a little from Algorithm 1: m = floor(sqrt n) columns of m
  * elements, the last one extended to the end of the node; m pivot samples
  * drawn once (no redraws) from the node's input before its columns are
- * sorted, the largest replaced by +inf and each sample equal to the next one
- * lowered to its predecessor in the (key, val) order; bucket i holds the
- * elements e with p_{i-1} < e <= p_i.  Integer keys only (SQ_U32, SQ_U64),
- * a cutoff of at least 3, and n < sq_max_n(dtype). */
+ * sorted, the largest replaced by the greatest (key, val) pair and each
+ * sample equal to the next one lowered to its predecessor in the (key, val)
+ * order; bucket i holds the elements e with p_{i-1} < e <= p_i; a bucket
+ * whose range holds a single pair (p_{i-1} the predecessor of p_i, or p_0 =
+ * the least pair (0, 0)) is copied, not sorted.  Integer keys only (SQ_U32,
+ * SQ_U64), a cutoff of at least 8 (so that every node draws m >= 3 samples),
+ * and n < sq_max_n(dtype).  Repeated (key, val) pairs are allowed. */
 typedef enum { SQ_ALGORITHM1 = 0, SQ_APPENDIX = 1 } sq_variant;
 
 typedef struct {

@@ -162,7 +162,7 @@ def sq_sort(keys, vals=None, seed: int = 0, dtype: str | None = None, cutoff: in
     """Sort (keys, vals) in place (CUDA tensors, or CPU tensors / numpy arrays,
     which the library stages through device memory).  Returns the list of
     per-node trace records when ``trace_cap`` > 0, else None.  ``variant``:
-    "algorithm1" or "appendix" (integer keys, cutoff >= 3)."""
+    "algorithm1" or "appendix" (integer keys, cutoff >= 8)."""
     n = _numel(keys)
     if vals is not None and _numel(vals) != n:
         raise ValueError("keys and vals differ in length")

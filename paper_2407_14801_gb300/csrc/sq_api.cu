@@ -287,8 +287,8 @@ sq_status sq_sort_ex(void *keys, uint32_t *vals, uint64_t n, sq_dtype dtype, uin
   if (opts && opts->variant > SQ_APPENDIX) return fail(SQ_ERR_INVALID, "unknown variant %u", opts->variant);
   if (opts && opts->variant == SQ_APPENDIX) {
     if (dtype == SQ_F32) return fail(SQ_ERR_INVALID, "the appendix variant sorts integer keys");
-    if (opts->cutoff == 2 || (!opts->cutoff && cutoff_for(dtype, n) < 3))
-      return fail(SQ_ERR_INVALID, "the appendix variant needs a cutoff of at least 3");
+    if ((opts->cutoff && opts->cutoff < 8) || (!opts->cutoff && cutoff_for(dtype, n) < 8))
+      return fail(SQ_ERR_INVALID, "the appendix variant needs a cutoff of at least 8");
     if (n >= sq_max_n(dtype))
       return fail(SQ_ERR_INVALID, "n = %llu: the appendix variant takes n < %llu", (unsigned long long)n,
                   (unsigned long long)sq_max_n(dtype));

@@ -658,8 +658,8 @@ struct Engine {
     }
     for (u32 i = 0; i < ninst && !spec.skew_only; i++)
       if (spec.inst[i].variant &&
-          (spec.inst[i].n >= lim || cutoff_of(i) < 3 || (DT != DT_U32 && DT != DT_U64))) {
-        snprintf(err, errlen, "the appendix variant takes integer keys, n < %llu and a cutoff >= 3",
+          (spec.inst[i].n >= lim || cutoff_of(i) < 8 || (DT != DT_U32 && DT != DT_U64))) {
+        snprintf(err, errlen, "the appendix variant takes integer keys, n < %llu and a cutoff >= 8",
                  (unsigned long long)lim);
         return 1;
       }

@@ -957,10 +957,11 @@ __device__ __forceinline__ void trace_node(const Ctx &c, const Node *nd, u32 att
 
 // The pivot step of the paper's appendix listing: k (= m) samples drawn with
 // replacement from the node's input A (which the column sorts, writing D,
-// leave as it was), sorted; the largest becomes +inf (k-1 pivots remain);
-// a sample equal to the one after it is replaced by its predecessor (each
-// comparison with the sample as drawn: the listing lowers only the earlier
-// one of a pair).  One sample, no redraws.
+// leave as it was), sorted; the largest becomes the greatest pair, K::top()
+// (the listing's INT_MAX; it stays implicit: bucket k-1 takes everything
+// above pivot k-2); a sample equal to the one after it is replaced by its
+// predecessor (each comparison with the sample as drawn: the listing lowers
+// only the earlier one of a pair).  One sample, no redraws.
 template <class K, class S, int T, int R, bool WARP>
 __device__ __forceinline__ void pivots_appendix(const Ctx &c, Node *nd, typename K::elem_t *s, int tid) {
   typedef typename K::elem_t E;
@@ -999,15 +1000,19 @@ __device__ __forceinline__ void pivots_appendix(const Ctx &c, Node *nd, typename
 #pragma unroll
   for (int q = 0; q < R; q++) {
     const u32 r = tid * R + q;
-    if (r + 1 < ns) {  // (sample ns-1 is the +inf flag)
+    if (r + 1 < ns) {  // (sample ns-1 is now the greatest pair)
       E e = x[q];
-      if (r + 2 < ns && K::eq(e, q + 1 < R ? x[q + 1] : after)) e = pred_elem<K>(e);
+      const E nx = r + 2 < ns ? (q + 1 < R ? x[q + 1] : after) : K::top();
+      if (K::eq(e, nx)) e = pred_elem<K>(e);
       pk[r] = K::key(e);
       pv[r] = K::val(e);
     }
   }
   if (tid == 0) {
     nd->attempts = 1;
+    // one guard count per bucket chunk of k_expand_buckets (the columns are
+    // done: nothing else counts on pending until then)
+    nd->pending = (int)((nd->k + kExpandChunk - 1) / kExpandChunk);
     trace_node(c, nd, 1);
   }
   S::sync();  // the group is done with s before it takes the next node
@@ -2082,8 +2087,53 @@ __global__ void __launch_bounds__(256) k_copy_runs(const Ctx *__restrict__ cp) {
   }
 }
 
+// The appendix variant's monochromatic rule for bucket j of a node (see
+// k_expand_buckets), from the node's k-1 stored pivots.
+template <int DT>
+__device__ __forceinline__ bool mono_bucket(const u32 *meta, const MetaLayout &ML, u32 k, u32 j) {
+  typedef KT<DT> K;
+  typedef typename K::key_t key_t;
+  typedef typename K::elem_t E;
+  const key_t *pk = reinterpret_cast<const key_t *>(meta + ML.pk);
+  const u32 *pv = meta + ML.pv;
+  if (j == 0) return K::eq(K::make(pk[0], pv[0]), K::make(0, 0u));
+  const E lo = K::make(pk[j - 1], pv[j - 1]);
+  const E hi = j + 1 < k ? K::make(pk[j], pv[j]) : K::top();
+  return K::lt(lo, hi) && K::eq(pred_elem<K>(hi), lo);
+}
+
+// Copies the monochromatic buckets of one k_expand_buckets chunk (each thread
+// names its own, n = 0 for none) from A, where the SkewTranspose left them,
+// to the node's output (D, or the final buffer); the block takes them in turn.
+template <int DT>
+__device__ void copy_mono_buckets(const Inst &I, u32 out, u64 off, u32 n) {
+  typedef typename KT<DT>::key_t key_t;
+  __shared__ u64 s_off[kExpandChunk];
+  __shared__ u32 s_n[kExpandChunk];
+  if (threadIdx.x < kExpandChunk) {
+    s_off[threadIdx.x] = off;
+    s_n[threadIdx.x] = n;
+  }
+  __syncthreads();
+  const key_t *ak = (const key_t *)I.keys;
+  const u32 *av = I.vals;
+  key_t *ok = (key_t *)(out ? I.dkeys : I.fkeys);
+  u32 *ov = out ? I.dvals : I.fvals;
+  if ((const void *)ak != (const void *)ok || av != ov) {  // else already in place
+    for (int t = 0; t < kExpandChunk; t++) {
+      const u32 len = s_n[t];
+      const u64 o = s_off[t];
+      for (u32 i = threadIdx.x; i < len; i += blockDim.x) {
+        ok[o + i] = ak[o + i];
+        ov[o + i] = av[o + i];
+      }
+    }
+  }
+  __syncthreads();  // (s_off / s_n are reused by the block's next chunk)
+}
+
 // Bucket children of every ready node (Algorithm 1's last loop), spawned in
-// work items of kExpandChunk buckets.  Every bucket of a SquareSort node is
+// work items of kExpandChunk buckets.  Every bucket of an Algorithm 1 node is
 // non-empty (bucket j >= 1 holds pivot j, bucket 0 the minimum), so the node
 // waits for exactly k children.
 template <int DT>
@@ -2102,21 +2152,29 @@ __global__ void __launch_bounds__(256) k_expand_buckets(const Ctx *__restrict__ 
     const u32 *b = c.meta + nd.meta + ML.b;
     const u32 chunk = u - c.wbase[3ull * c.ready_cap + s_ri];
     // Under the appendix variant a bucket may be empty (a pivot lowered to
-    // its predecessor need not be an element of the node); the node then
-    // waits for its non-empty buckets only, which every chunk adds to its
-    // pending count (zero since its last column finished; its children
-    // start in the next round).
-    const bool var = c.inst[nd.inst].variant == VAR_APPENDIX;
+    // its predecessor need not be an element of the node), and a bucket
+    // whose range holds a single (key, val) pair -- bucket j > 0 with pivot
+    // j-1 the predecessor of pivot j (pivot k-1 the greatest pair), or bucket
+        // 0 with pivot 0 the least pair -- holds only copies of it and is copied
+    // to the node's output instead of sorted.  The node then waits for its
+    // other buckets only, which every chunk adds to its pending count (the
+    // pivot step set one guard per chunk; its children start in the next
+    // round).
+    const Inst I = c.inst[nd.inst];
+    const bool var = I.variant == VAR_APPENDIX;
     if (!var && chunk == 0 && threadIdx.x == 0) c.nodes[id].pending = (int)nd.k;
     const u32 j = chunk * kExpandChunk + threadIdx.x;
     Child ch;
-    bool has = false;
+    bool has = false, mono = false;
     if (threadIdx.x < kExpandChunk && j < nd.k) {
       ch.n = b[j + 1] - b[j];
       has = true;
       if (ch.n == 0) {
         if (!var) atomicOr(&c.status->error, ERRB_SIZES);  // cannot happen for a valid Algorithm 1 sample
         has = false;
+      } else if (var) {
+        mono = mono_bucket<DT>(c.meta + nd.meta, ML, nd.k, j);
+        has = !mono;
       }
       ch.off = nd.off + b[j];
       ch.hash = buc_hash(nd.hash, j);
@@ -2129,8 +2187,13 @@ __global__ void __launch_bounds__(256) k_expand_buckets(const Ctx *__restrict__ 
       ch.src = 0;  // a bucket reads what its parent's SkewTranspose wrote
     }
     if (var) {
-      const int nonempty = __syncthreads_count(has);
-      if (threadIdx.x == 0 && nonempty) atomicAdd(&c.nodes[id].pending, nonempty);
+      // this chunk's waiting buckets replace its guard count; the last chunk
+      // of a node none of whose buckets waits reports the node complete (its
+      // copies are in place when the next kernel starts)
+      const int waits = __syncthreads_count(has);
+      if (__syncthreads_or(mono)) copy_mono_buckets<DT>(I, nd.out, mono ? nd.off + b[j] : 0, mono ? ch.n : 0);
+      if (threadIdx.x == 0 && atomicAdd(&c.nodes[id].pending, waits - 1) + waits - 1 == 0)
+        child_done(c, nd.parent, nd.kind, nd.inst);
     }
     spawn_batch(c, has, ch, c.fresh_cur, &c.cnt_cur->fresh, LeafCfg<DT>::nclass);
   }

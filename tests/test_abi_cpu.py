@@ -66,7 +66,7 @@ def test_rejects_bad_arguments_without_a_device(sq):
 
 
 def test_appendix_variant_refusals_without_a_device(sq):
-    """The variant takes integer keys, a cutoff of at least 3 and n below
+    """The variant takes integer keys, a cutoff of at least 8 and n below
     sq_max_n; the checks come before any device work."""
     L = sq.lib()
 
@@ -75,7 +75,7 @@ def test_appendix_variant_refusals_without_a_device(sq):
         return L.sq_sort_ex(ctypes.c_void_p(8), None, n, dtype, 0, None, ctypes.byref(opts))
 
     assert ex(2, 10, 16, 1) == 1 and b"integer" in L.sq_last_error()  # SQ_F32
-    assert ex(0, 10, 2, 1) == 1 and b"cutoff" in L.sq_last_error()
+    assert ex(0, 10, 7, 1) == 1 and b"cutoff" in L.sq_last_error()
     assert ex(0, 10, 16, 2) == 1 and b"variant" in L.sq_last_error()
     assert ex(0, sq.max_n("u32"), 16, 1) == 1 and b"appendix" in L.sq_last_error()
     assert ex(1, sq.max_n("u64"), 16, 1) == 1

@@ -64,13 +64,11 @@ SIZES = [1, 2, 3, 4, 8, 9, 15, 16, 17, 63, 64, 65, 100, 511, 513, 1000, 2048, 20
          32769, 50000, 65536, 65537, 200003, 1000003]
 
 
-@pytest.mark.parametrize("cutoff", [3, 4, 16, 64, 512, 8192, 65536])
+@pytest.mark.parametrize("cutoff", [8, 9, 16, 64, 512, 8192, 65536])
 def test_u32_uniform_all_sizes(sq, cutoff):
     nodes = 0
     for n in SIZES:
-        if (cutoff <= 4 and n > 50000) or (cutoff <= 64 and n > 200003):
-            continue
-        if n <= 2 and cutoff < n:
+        if (cutoff <= 9 and n > 50000) or (cutoff <= 64 and n > 200003):
             continue
         perm = np.random.default_rng(n).permutation(n).astype(np.uint32)
         nodes += check(sq, W.uniform_u32(n, 300 + n), perm, "u32", seed=n + cutoff, cutoff=cutoff)
@@ -96,19 +94,19 @@ def distribution(name, n, seed):
 
 
 @pytest.mark.parametrize("name", ["alphabet", "one_key", "sorted", "reverse", "extremes"])
-@pytest.mark.parametrize("cutoff", [3, 16, 700, 65536])
+@pytest.mark.parametrize("cutoff", [8, 16, 700, 65536])
 def test_u32_distributions(sq, name, cutoff):
     for n in [1000, 65536, 300001, 2000000]:
-        if (cutoff == 3 and n > 65536) or (cutoff == 16 and n > 300001):
+        if (cutoff == 8 and n > 65536) or (cutoff == 16 and n > 300001):
             continue
         keys, vals = distribution(name, n, 11 + n)
         check(sq, keys, vals, "u32", seed=5, cutoff=cutoff)
 
 
-@pytest.mark.parametrize("cutoff", [3, 64, 8192])
+@pytest.mark.parametrize("cutoff", [8, 64, 8192])
 def test_u64_keys(sq, cutoff):
     for n in [17, 5000, 100000, 1000003]:
-        if cutoff == 3 and n > 100000:
+        if cutoff == 8 and n > 100000:
             continue
         check(sq, W.zipf_u64(n, n), W.iota(n), "u64", seed=7, cutoff=cutoff)
         check(sq, W.uniform_u64(n, n + 1), np.random.default_rng(n).permutation(n).astype(np.uint32), "u64",
@@ -150,7 +148,61 @@ def test_refusals(sq):
     with pytest.raises(RuntimeError):
         sq.sort(torch.zeros(100, dtype=torch.float32, device="cuda"), None, cutoff=16, variant="appendix")
     with pytest.raises(RuntimeError):
-        sq.sort(torch.zeros(100, dtype=torch.int32, device="cuda"), None, dtype="u32", cutoff=2,
+        sq.sort(torch.zeros(100, dtype=torch.int32, device="cuda"), None, dtype="u32", cutoff=7,
                 variant="appendix")
     with pytest.raises(ValueError):
         sq.sort(torch.zeros(100, dtype=torch.int32, device="cuda"), None, dtype="u32", variant="listing")
+
+
+TOP = {"u32": (0xFFFFFFFF, 0xFFFFFFFF), "u64": (2**64 - 1, 0xFFFFFFFF)}
+
+
+def repeated_pair_inputs(n):
+    """Inputs whose (key, val) pairs repeat: buckets that hold one pair are
+    copied, at the least pair, the greatest, and in between."""
+    g = np.random.default_rng(n)
+    for dt in ("u32", "u64"):
+        kdt = np.uint32 if dt == "u32" else np.uint64
+        for k, v in [(0, 0), TOP[dt], (5, 7)]:
+            yield dt, np.full(n, k, dtype=kdt), np.full(n, v, dtype=np.uint32)
+    keys = g.integers(0, 6, size=n).astype(np.uint32)
+    vals = g.integers(0, 3, size=n).astype(np.uint32)
+    yield "u32", keys, vals
+    k2, v2 = keys.copy(), vals.copy()
+    k2[: n // 40], v2[: n // 40] = TOP["u32"]  # a few copies of the greatest pair
+    yield "u32", k2, v2
+    k3, v3 = keys.copy(), vals.copy()
+    k3[: n // 2], v3[: n // 2] = 0, 0  # half the input the least pair
+    yield "u32", k3, v3
+    yield "u64", W.zipf_u64(n, n).copy(), np.zeros(n, dtype=np.uint32)
+
+
+@pytest.mark.parametrize("cutoff", [8, 16, 100, 65536])
+def test_repeated_pairs_match_the_oracle(sq, cutoff):
+    for n in [9, 1000, 65536, 1 << 20]:
+        if cutoff <= 16 and n > 65536:
+            continue
+        for dt, keys, vals in repeated_pair_inputs(n):
+            check(sq, keys, vals, dt, seed=n + cutoff, cutoff=cutoff)
+
+
+def test_repeated_pairs_from_pinned_host_buffers(sq):
+    """Host buffers: the first pass reads them and the last writes them in
+    place, so a copied bucket goes to the host buffer too."""
+    n = 1 << 20
+    for dt, keys, vals in repeated_pair_inputs(n):
+        view, back = VIEW[dt]
+        hk = torch.from_numpy(keys.view(view).copy()).pin_memory()
+        hv = torch.from_numpy(vals.view(np.int32).copy()).pin_memory()
+        sq.sort(hk, hv, seed=3, dtype=dt, cutoff=256, variant="appendix")
+        o = np.lexsort((vals, keys))
+        assert (hk.numpy().view(back) == keys[o]).all() and (hv.numpy().view(np.uint32) == vals[o]).all(), dt
+
+
+def test_repeated_pairs_in_graph_launch_mode(sq):
+    sq.set_launch_mode("graph")
+    try:
+        for dt, keys, vals in repeated_pair_inputs(300001):
+            check(sq, keys, vals, dt, seed=9, cutoff=64)
+    finally:
+        sq.set_launch_mode("auto")
