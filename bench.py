@@ -242,7 +242,7 @@ def bench_plain(args, sq, dist, rank, world, local):
     stream = torch.cuda.current_stream()
     cutoff = args.cutoff
     for i in range(args.warmup):
-        sq.sort(keys[i], vals[i], seed=i, dtype="u32", cutoff=cutoff)
+        sq.sort(keys[i], vals[i], seed=i, dtype="u32", cutoff=cutoff, variant=args.variant)
     torch.cuda.synchronize()
     sq.reset_stats()
     clocks = make_clocks(local)
@@ -256,7 +256,7 @@ def bench_plain(args, sq, dist, rank, world, local):
     ev0.record(stream)
     t_wall0 = time.perf_counter()
     for i in range(args.warmup, total):
-        sq.sort(keys[i], vals[i], seed=i, dtype="u32", cutoff=cutoff)
+        sq.sort(keys[i], vals[i], seed=i, dtype="u32", cutoff=cutoff, variant=args.variant)
     ev1.record(stream)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
@@ -278,12 +278,12 @@ def bench_plain(args, sq, dist, rank, world, local):
             vals[i].copy_(iota)
         torch.cuda.synchronize()
         for i in range(args.warmup, total):
-            sq.sort(keys[i], vals[i], seed=i, dtype="u32", cutoff=cutoff)
+            sq.sort(keys[i], vals[i], seed=i, dtype="u32", cutoff=cutoff, variant=args.variant)
 
     st = profiled(sq, again)
     del keys, vals
     torch.cuda.empty_cache()
-    workload_name = f"plain_u32_n{n}"
+    workload_name = f"plain_u32_n{n}" + ("" if args.variant == "algorithm1" else f"_{args.variant}")
     roofline = roofline_of(st, workload_name, "a profiling pass over the same sorts after the timed region")
     peak = roofline["peak"]
     # whole-step roofline against the ideal one-level traffic 6 w n (w = 8 bytes)
@@ -292,7 +292,7 @@ def bench_plain(args, sq, dist, rank, world, local):
     # end to end through the C ABI with host (pinned) buffers
     e2e = None
     if not args.no_e2e:
-        e2e = bench_e2e(sq, n, min(args.steps, 4), dev, inputs)
+        e2e = bench_e2e(sq, n, min(args.steps, 4), dev, inputs, args.variant)
     del inputs
     torch.cuda.empty_cache()
 
@@ -305,6 +305,7 @@ def bench_plain(args, sq, dist, rank, world, local):
                    "distribution_seeds": {d: DIST_SEED[d] for d in dists},
                    "step_cycle": f"step i sorts distribution i mod {len(dists)}",
                    "cutoff": sq.get_cutoff("u32") if not cutoff else cutoff,
+                   "variant": args.variant,
                    "l2": "inputs larger than L2 (each step sorts its own 2 GiB copy)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,
@@ -442,7 +443,7 @@ def bench_wide(args, sq, dist, rank, world, local):
     }
 
 
-def bench_e2e(sq, n, steps, dev, inputs):
+def bench_e2e(sq, n, steps, dev, inputs, variant="algorithm1"):
     import torch
 
     hk = torch.empty(n, dtype=torch.int32).pin_memory()
@@ -453,7 +454,7 @@ def bench_e2e(sq, n, steps, dev, inputs):
     for i in range(2):  # untimed: the first calls grow the device memory pool
         hk.copy_(src[names[i % len(src)]])
         hv.copy_(iota)
-        sq.sort(hk, hv, seed=90 + i, dtype="u32")
+        sq.sort(hk, hv, seed=90 + i, dtype="u32", variant=variant)
     tot = 0.0
     for i in range(steps):
         d = names[i % len(names)]
@@ -461,14 +462,14 @@ def bench_e2e(sq, n, steps, dev, inputs):
         hv.copy_(iota)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        sq.sort(hk, hv, seed=100 + i, dtype="u32")  # H2D, sort, D2H inside the call
+        sq.sort(hk, hv, seed=100 + i, dtype="u32", variant=variant)  # H2D, sort, D2H inside the call
         tot += time.perf_counter() - t0
     return {"value": round(steps * n / tot / 1e9, 3), "unit": UNIT, "h2d_bytes_per_step": 8 * n,
             "d2h_bytes_per_step": 8 * n, "steps": steps, "warmup": 2,
             "buffers": "pinned host, read by the first pass and written by the last through the device mapping"}
 
 
-def cpu_baseline(sample_log2: int = 23, budget_s: float = 25.0):
+def cpu_baseline(sample_log2: int = 23, budget_s: float = 25.0, variant: str = "algorithm1"):
     """The CPU oracle, single-threaded, on a bounded sample of the workload:
     the first 2^sample_log2 keys of each distribution's generator."""
     import numpy as np
@@ -484,14 +485,14 @@ def cpu_baseline(sample_log2: int = 23, budget_s: float = 25.0):
         k = gens[d](n, DIST_SEED[d])
         v = W.iota(n)
         t0 = time.perf_counter()
-        oracle.sort(k, v, seed=1, cutoff=16384)
+        oracle.sort(k, v, seed=1, cutoff=16384, variant=variant)
         t += time.perf_counter() - t0
         done += n
         if t > budget_s:
             break
     return {"value": round(done / t / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{done // n} x 2^{sample_log2} uint32 keys (first keys of each distribution's generator), "
-                      f"cutoff 16384, single thread", "seconds": round(t, 2)}
+                      f"cutoff 16384, {variant}, single thread", "seconds": round(t, 2)}
 
 
 def cpu_baseline_wide(sample_log2: int = 21, budget_s: float = 20.0):
@@ -530,7 +531,7 @@ def run_ours(args):
     if args.workload == "plain":
         out = bench_plain(args, sq, dist, rank, world, local)
         if rank == 0 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline()
+            out["cpu_baseline"] = cpu_baseline(variant=args.variant)
     elif args.workload == "wide":
         out = bench_wide(args, sq, dist, rank, world, local)
         if rank == 0 and not args.no_cpu_baseline:
@@ -997,6 +998,8 @@ def main():
     ap.add_argument("--workload", default="plain", choices=["plain", "wide", "batch", "serve"])
     ap.add_argument("--n", type=int, default=1 << 28)
     ap.add_argument("--cutoff", type=int, default=0)
+    ap.add_argument("--variant", default="algorithm1", choices=["algorithm1", "appendix"],
+                    help="plain workload: Algorithm 1, or the variant of the paper's appendix code")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-count", type=int, default=4096)
