@@ -1149,20 +1149,64 @@ __global__ void __launch_bounds__(WARP ? 256 : T) k_pivots(const Ctx *__restrict
   }
 }
 
+// Exclusive prefix sum over a warp (and the warp total).
+__device__ __forceinline__ u32 warp_excl_scan(u32 v, u32 &total) {
+  const int lane = threadIdx.x & 31;
+  u32 inc = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const u32 o = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= d) inc += o;
+  }
+  total = __shfl_sync(0xffffffffu, inc, 31);
+  return inc - v;
+}
+
 // ----------------------------------------------------------------- count ---
 // One pass over the sorted columns of a block of kCountCols columns
 // (Section 2.2: each sorted column is scanned against the sorted pivots).
-// Every warp streams a contiguous part of the block in groups of 32*kCountR
-// elements, kCountR consecutive ones a lane.  Within a column the group's
-// buckets lie between the previous group's last bucket and the bucket of the
-// group's last element (found by a warp-wide probe); a lane searches that
-// range for its first element and gallops from there for the others.
-// Produces the block's per-bucket totals T[I][j], per column the start
-// P[Jb][i] of every kSkewBkts-bucket segment, and every element's tag (its
-// bucket within its segment) for the SkewTranspose.
+// The block's columns are cut into warp chunks of 32*kCountE elements that
+// never cross a column end; every warp takes a contiguous run of chunks,
+// kCountE consecutive elements a lane.  A chunk's buckets run from its first
+// element's (carried from the warp's previous chunk of the column) to the
+// next element's (one warp-wide probe); a chunk with no pivot in that range
+// is one bucket and costs no search at all.  Otherwise a lane finds its first
+// element's bucket by binary search within the chunk's range and steps over
+// the pivots below each next element.  Produces the block's per-bucket totals
+// T[I][j], per column the start P[Jb][i] of every kSkewBkts-bucket segment
+// (the first position whose bucket is at least Jb*kSkewBkts; the column's
+// length past its last bucket), and every element's tag (its bucket within
+// its segment) for the SkewTranspose.
 
-constexpr int kCountR = 4;  // count: consecutive elements a lane
+constexpr int kCountE = 8;     // count: consecutive elements a lane
+constexpr int kCountStep = 8;  // count: pivots stepped over one by one before a binary search
 constexpr u32 kPiece = 256;  // skew: elements per warp work piece
+
+// Bucket of an element that every lane of the warp holds, among the pivots
+// piv[lo, hi) (the result is in [lo, hi]): 32-way probes, narrowing the range
+// 32-fold a round.
+template <class K>
+__device__ __forceinline__ int warp_bucket_in(const typename K::elem_t *piv, int lo, int hi,
+                                              const typename K::elem_t &e, bool le) {
+  const int lane = threadIdx.x & 31;
+  while (hi - lo > 32) {
+    const int step = (hi - lo + 31) >> 5;
+    const int idx = lo + (lane + 1) * step - 1;
+    const bool nb = idx < hi && !below_p<K>(e, piv[idx], le);
+    const int cnt = __popc(__ballot_sync(0xffffffffu, nb));
+    lo = min(lo + cnt * step, hi);
+    hi = min(hi, lo + step - 1);
+  }
+  const bool nb = lo + lane < hi && !below_p<K>(e, piv[lo + lane], le);
+  return lo + __popc(__ballot_sync(0xffffffffu, nb));
+}
+
+// P[Jb][col] = pos for the segments that start between a bucket bp (-1 before
+// a column's first element) and a bucket b >= bp: Jb in (bp/64, b/64].
+__device__ __forceinline__ void count_seg_starts(u32 *P, u32 cols, u32 col, int bp, int b, u32 pos) {
+  for (int Jb = (bp + (int)kSkewBkts) / (int)kSkewBkts; Jb <= b / (int)kSkewBkts; ++Jb)
+    P[(u64)Jb * cols + col] = pos;
+}
 
 template <int DT>
 __global__ void __launch_bounds__(1024) k_count(const Ctx *__restrict__ cp, u32 ready_count, u32 kmax) {
@@ -1171,10 +1215,14 @@ __global__ void __launch_bounds__(1024) k_count(const Ctx *__restrict__ cp, u32 
   typedef KT<DT> K;
   typedef typename K::elem_t E;
   typedef typename K::key_t key_t;
+  constexpr int EL = sizeof(E) > 8 ? kCountE / 2 : kCountE;  // (three-word elements: half, within 64 registers)
+  constexpr u32 CH = 32 * EL;  // elements of a warp chunk
+  static_assert(EL % 4 == 0, "128-bit payload loads and word tag stores take 4 elements at a time");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   E *piv = reinterpret_cast<E *>(smem_raw);
   u32 *hist = reinterpret_cast<u32 *>(piv + (kmax > 1 ? kmax - 1 : 1));
   __shared__ u32 s_u, s_ri;
+  __shared__ u32 s_cpre[kCountCols + 1];  // chunks before each column of the block
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int NT = blockDim.x, NW = NT >> 5;
   u32 cur = kNone;
@@ -1194,7 +1242,6 @@ __global__ void __launch_bounds__(1024) k_count(const Ctx *__restrict__ cp, u32 
       cur = id;
     }
     for (u32 j = tid; j < nd.k; j += NT) hist[j] = 0;
-    __syncthreads();
     const Inst I = c.inst[nd.inst];
     const key_t *dk = (const key_t *)I.dkeys + nd.off;
     const u32 *dv = I.dvals + nd.off;
@@ -1204,136 +1251,152 @@ __global__ void __launch_bounds__(1024) k_count(const Ctx *__restrict__ cp, u32 
     const bool le = I.variant == VAR_APPENDIX;  // buckets bounded above by "<="
     const u32 Iblk = u - nd.unit_base;
     const u32 i0 = Iblk * kCountCols;
-    const u32 i1 = min(cols, i0 + kCountCols);
-    const u32 q0 = (u32)col_begin(i0, rows, n);
-    const u32 q1 = i1 >= cols ? n : (u32)col_begin(i1, rows, n);
-    const u32 S = q1 - q0;
-    constexpr int CR = kCountR;  // consecutive elements a lane, kCountR * 32 a warp group
-    const u32 per_warp = (((S + NW - 1) / NW) + 32 * CR - 1) / (32 * CR) * (32 * CR);
-    const u32 ws = q0 + min(S, warp * per_warp);
-    const u32 we = q0 + min(S, warp * per_warp + per_warp);
-    // column ci and offset pos of this lane's first element, advanced 32*CR per group
-    const u32 p_l = ws + (u32)(CR * lane);
-    u32 ci = min(p_l / rows, cols - 1), pos = p_l - ci * rows;  // (the last column runs to n)
-    int carry_b = -1;
-    u32 carry_i = kNone;
-    for (u32 gs = ws; gs < we; gs += 32 * CR) {
-      const u32 pl = gs + (u32)(CR * lane);  // this lane's elements: [pl, pl + CR) within [gs, we)
-      E ev[CR];
-#pragma unroll
-      for (int r = 0; r < CR; r++) ev[r] = pl + r < we ? K::make(dk[pl + r], dv[pl + r]) : K::top();
-      const u32 glast = min(we, gs + 32 * CR) - 1;  // the group's last element
-      const int llast = (int)((glast - gs) / CR), rlast = (int)((glast - gs) % CR);
-      // the column of every element of the lane (a lane crosses at most a few column ends)
-      u32 cr[CR], pr[CR];
-      {
-        u32 c2 = ci, p2 = pos;
-#pragma unroll
-        for (int r = 0; r < CR; r++) {
-          while (p2 >= rows && c2 + 1 < cols) {
-            p2 -= rows;
-            ++c2;
-          }
-          cr[r] = c2;
-          pr[r] = p2;
-          ++p2;
-        }
+    const u32 nc = min(cols, i0 + kCountCols) - i0;
+    if (warp == 0) {
+      u32 nch = 0;
+      if ((u32)lane < nc) {
+        const u32 i = i0 + lane;
+        nch = (u32)((col_end(i, rows, cols, n) - col_begin(i, rows, n) + CH - 1) / CH);
       }
-      u32 my_last_c = cr[0];
-      E my_last_e = ev[0];
+      u32 tot;
+      const u32 ex = warp_excl_scan(nch, tot);
+      if ((u32)lane <= nc) s_cpre[lane] = ex;  // (lane nc: the block's total)
+    }
+    __syncthreads();
+    const u32 nck = s_cpre[nc];
+    const u32 cw0 = (u32)((u64)nck * warp / NW), cw1 = (u32)((u64)nck * (warp + 1) / NW);
+    u32 ci = 0;  // column (within the block) of chunk ck
+    int lo = -1, bprev = -1;  // bucket of the chunk's first element and of the element before it
+    for (u32 ck = cw0; ck < cw1; ++ck) {
+      bool fresh = ck == cw0;
+      while (s_cpre[ci + 1] <= ck) {
+        ++ci;
+        fresh = true;
+      }
+      const u32 col = i0 + ci;
+      const u32 cb = (u32)col_begin(col, rows, n), ce = (u32)col_end(col, rows, cols, n);
+      const u32 off = (ck - s_cpre[ci]) * CH;  // chunk start within the column
+      const u32 g0 = cb + off;
+      const u32 na = min(CH, ce - g0);  // elements in the chunk
+      const u32 p0 = g0 + (u32)lane * EL;
+      E ev[EL];
+      if ((u32)(lane + 1) * EL <= na && (((uintptr_t)(dk + p0) | (uintptr_t)(dv + p0)) & 15) == 0) {
+        // whole and 16-byte aligned (the same for every lane): 128-bit loads
+        key_t kk[EL];
+        u32 vv[EL];
 #pragma unroll
-      for (int r = 1; r < CR; r++)
-        if (r == rlast) {
-          my_last_c = cr[r];
-          my_last_e = ev[r];
+        for (int q = 0; q < (int)(sizeof(key_t) * EL / 16); q++)
+          reinterpret_cast<uint4 *>(kk)[q] = __ldg(reinterpret_cast<const uint4 *>(dk + p0) + q);
+#pragma unroll
+        for (int q = 0; q < EL / 4; q++) reinterpret_cast<uint4 *>(vv)[q] = __ldg(reinterpret_cast<const uint4 *>(dv + p0) + q);
+#pragma unroll
+        for (int r = 0; r < EL; r++) ev[r] = K::make(kk[r], vv[r]);
+      } else {
+#pragma unroll
+        for (int r = 0; r < EL; r++)
+          ev[r] = (u32)lane * EL + r < na ? K::make(dk[p0 + r], dv[p0 + r]) : K::top();
+      }
+      if (fresh) {  // the warp's first chunk in this column: search
+        lo = warp_bucket_in<K>(piv, 0, np, shfl_e(ev[0], 0), le);
+        bprev = -1;
+        if (off) bprev = warp_bucket_in<K>(piv, 0, lo, K::make(dk[g0 - 1], dv[g0 - 1]), le);
+      }
+      const u32 llast = (na - 1) / EL, rlast = (na - 1) % EL;  // lane and slot of the last element
+      const bool last_chunk = g0 + na == ce;
+      // bucket of the element after the chunk (of its last element, for a column's last chunk)
+      E mine = ev[0];
+#pragma unroll
+      for (int r = 1; r < EL; r++)
+        if ((u32)r == rlast) mine = ev[r];
+      const E elast = shfl_e(mine, llast);
+      const E enx = last_chunk ? elast : K::make(dk[g0 + na], dv[g0 + na]);
+      const int hn = warp_bucket_from<K, 16>(piv, lo, np, enx, le);
+      const u32 nv = (u32)lane * EL < na ? min((u32)EL, na - (u32)lane * EL) : 0u;  // the lane's elements
+      int blast;  // bucket of the chunk's last element
+      if (lo == hn) {  // one bucket: no pivot between the chunk's first element and the next
+        if (lane == 0) {
+          atomicAdd(&hist[lo], na);
+          count_seg_starts(P, cols, col, bprev, lo, off);
         }
-      const u32 i_first = __shfl_sync(0xffffffffu, ci, 0);
-      const u32 i_last = __shfl_sync(0xffffffffu, my_last_c, llast);
-      int bk[CR];
-      if (i_first == i_last) {  // one column: buckets ascend through the group
-        const int lo = i_first == carry_i ? carry_b : 0;
-        const E elast = shfl_e(my_last_e, llast);
-        const int hi = warp_bucket_from<K, 4 * CR>(piv, lo, np, elast, le);
-        bk[0] = upper_bound_e<K>(piv, lo, hi, ev[0], le);
+        if (tg && nv) {
+          uint8_t *tp = tg + p0;
+          const u32 t = (u32)(lo & (kSkewBkts - 1)) * 0x01010101u;
+          if (nv == EL && ((uintptr_t)tp & 3) == 0) {
 #pragma unroll
-        for (int r = 1; r < CR; r++) {  // gallop from the previous element's bucket
-          int lo2 = bk[r - 1], st = 1, b = hi;
-          for (;;) {
-            const int idx = lo2 + st - 1;
-            if (idx >= hi) {
-              b = upper_bound_e<K>(piv, lo2, hi, ev[r], le);
-              break;
-            }
-            if (below_p<K>(ev[r], piv[idx], le)) {
-              b = upper_bound_e<K>(piv, lo2, idx, ev[r], le);
-              break;
-            }
-            lo2 = idx + 1;
-            st <<= 1;
+            for (int w = 0; w < EL / 4; w++) reinterpret_cast<u32 *>(tp)[w] = t;
+          } else {
+            for (u32 r = 0; r < nv; r++) tp[r] = (uint8_t)t;
+          }
+        }
+        blast = lo;
+      } else {
+        int bk[EL];
+        int b = lane == 0 ? lo : (nv ? upper_bound_e<K>(piv, lo, hn, ev[0], le) : hn);
+#pragma unroll
+        for (int r = 0; r < EL; r++) {
+          // up to kCountStep pivots stepped over one by one, a binary search past
+          // that (a column of few distinct keys jumps over many pivots at once)
+          if ((u32)r < nv) {
+            const int lim = min(hn, b + kCountStep);
+            while (b < lim && !below_p<K>(ev[r], piv[b], le)) ++b;
+            if (b == lim && b < hn && !below_p<K>(ev[r], piv[b], le)) b = upper_bound_e<K>(piv, b + 1, hn, ev[r], le);
           }
           bk[r] = b;
         }
-      } else {
+        // segment starts: at the lane's first element from the previous lane's last
+        // bucket (the chunk's bprev for lane 0), then wherever the lane's buckets
+        // enter a new segment
+        int bp = __shfl_up_sync(0xffffffffu, bk[EL - 1], 1);
+        if (lane == 0) bp = bprev;
+        if (nv) {
+          const u32 q0 = off + (u32)lane * EL;
+          if (bp < 0 || (bp >> 6) != (bk[0] >> 6)) count_seg_starts(P, cols, col, bp, bk[0], q0);
 #pragma unroll
-        for (int r = 0; r < CR; r++) bk[r] = upper_bound_e<K>(piv, 0, np, ev[r], le);
-      }
-      // the bucket before the lane's first element (in its column; -1 at a column start)
-      int bprev = __shfl_up_sync(0xffffffffu, bk[CR - 1], 1);
-      if (lane == 0) {
-        if (carry_i == cr[0]) {
-          bprev = carry_b;
-        } else if (pr[0] != 0 && pl < we) {  // first element of this warp's range, mid-column
-          const E pe = K::make(dk[pl - 1], dv[pl - 1]);
-          bprev = upper_bound_e<K>(piv, 0, np, pe, le);
+          for (int r = 1; r < EL; r++)
+            if ((u32)r < nv && (bk[r - 1] >> 6) != (bk[r] >> 6)) count_seg_starts(P, cols, col, bk[r - 1], bk[r], q0 + r);
+          // bucket totals: one shared atomic per run of equal buckets in the lane
+          int runb = bk[0];
+          u32 runc = 1;
+#pragma unroll
+          for (int r = 1; r < EL; r++) {
+            if ((u32)r >= nv) break;
+            if (bk[r] != runb) {
+              atomicAdd(&hist[runb], runc);
+              runb = bk[r];
+              runc = 0;
+            }
+            ++runc;
+          }
+          atomicAdd(&hist[runb], runc);
+          if (tg) {
+            uint8_t *tp = tg + p0;
+            if (nv == EL && ((uintptr_t)tp & 3) == 0) {
+#pragma unroll
+              for (int w = 0; w < EL / 4; w++) {
+                u32 wv = 0;
+#pragma unroll
+                for (int r = 0; r < 4; r++) wv |= (u32)(bk[4 * w + r] & (kSkewBkts - 1)) << (8 * r);
+                reinterpret_cast<u32 *>(tp)[w] = wv;
+              }
+            } else {
+#pragma unroll
+              for (int r = 0; r < EL; r++)
+                if ((u32)r < nv) tp[r] = (uint8_t)(bk[r] & (kSkewBkts - 1));
+            }
+          }
         }
-      }
-      int lastb = bk[0];
+        int lb = bk[0];
 #pragma unroll
-      for (int r = 1; r < CR; r++)
-        if (r == rlast) lastb = bk[r];
-      const u32 nv = pl < we ? min((u32)CR, we - pl) : 0u;  // the lane's valid elements
-      if (tg) {  // tags for the SkewTranspose: one word when the lane's four are whole and aligned
-        uint8_t *tp = tg + pl;
-        if (CR == 4 && nv == 4 && ((uintptr_t)tp & 3) == 0) {
-          u32 wv = 0;
-#pragma unroll
-          for (int r = 0; r < CR; r++) wv |= (u32)(bk[r] & (kSkewBkts - 1)) << (8 * r);
-          *reinterpret_cast<u32 *>(tp) = wv;
-        } else {
-#pragma unroll
-          for (int r = 0; r < CR; r++)
-            if ((u32)r < nv) tp[r] = (uint8_t)(bk[r] & (kSkewBkts - 1));
-        }
+        for (int r = 1; r < EL; r++)
+          if ((u32)r == rlast) lb = bk[r];
+        blast = __shfl_sync(0xffffffffu, lb, llast);
       }
-      int runb = -1;
-      u32 runc = 0;
-#pragma unroll
-      for (int r = 0; r < CR; r++) {
-        if ((u32)r >= nv) break;
-        const int b = bk[r];
-        if (b != runb) {  // bucket totals: one atomic per run of equal buckets in the lane
-          if (runc) atomicAdd(&hist[runb], runc);
-          runb = b;
-          runc = 0;
-        }
-        ++runc;
-        // segment starts P[Jb][i]: the first position whose bucket reaches Jb*kSkewBkts
-        const u32 c2 = cr[r], q = pr[r];
-        const int bp = q == 0 ? -1 : (r > 0 ? bk[r - 1] : bprev);
-        const u32 jb1 = (u32)b / kSkewBkts;
-        for (u32 Jb = (u32)(bp + kSkewBkts) / kSkewBkts; Jb <= jb1; ++Jb) P[(u64)Jb * cols + c2] = q;
-        const u32 len = (u32)(col_end(c2, rows, cols, n) - c2 * rows);  // (c2 * rows <= q's position < n)
-        if (q + 1 == len)
-          for (u32 Jb = jb1 + 1; Jb < nkb; ++Jb) P[(u64)Jb * cols + c2] = len;
+      if (last_chunk) {  // segments past the column's last bucket start at its end
+        const u32 len = ce - cb;
+        for (int Jb = blast / (int)kSkewBkts + 1 + lane; Jb < (int)nkb; Jb += 32) P[(u64)Jb * cols + col] = len;
       }
-      if (runc) atomicAdd(&hist[runb], runc);
-      carry_b = __shfl_sync(0xffffffffu, lastb, llast);
-      carry_i = i_last;
-      pos += 32 * CR;
-      while (pos >= rows && ci + 1 < cols) {
-        pos -= rows;
-        ++ci;
-      }
+      bprev = blast;
+      lo = hn;
     }
     __syncthreads();
     u32 *T = meta + ML.T;
@@ -1441,17 +1504,6 @@ struct SkewSmem {
   u32 s_u, s_ri, s_S;
 };
 
-__device__ __forceinline__ u32 warp_excl_scan(u32 v, u32 &total) {
-  const int lane = threadIdx.x & 31;
-  u32 inc = v;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const u32 o = __shfl_up_sync(0xffffffffu, inc, d);
-    if (lane >= d) inc += o;
-  }
-  total = __shfl_sync(0xffffffffu, inc, 31);
-  return inc - v;
-}
 
 template <int DT, int CAP, bool TAGS>
 __global__ void __launch_bounds__(256) k_skew(const Ctx *__restrict__ cp, u32 ready_count) {
