@@ -1702,7 +1702,7 @@ __global__ void __launch_bounds__(256) k_skew(const Ctx *__restrict__ cp, u32 re
 // one scan over the (tag, warp) counters gives every element its slot in
 // shared memory, and the chunk leaves with one coalesced run per bucket.
 #ifndef SQ_SKEW_WARPS
-#define SQ_SKEW_WARPS 4  // warps of a SkewTranspose CTA (each ranks 256 elements of a chunk)
+#define SQ_SKEW_WARPS 2  // warps of a SkewTranspose CTA (each ranks 256 elements of a chunk)
 #endif
 constexpr u32 kSkewBig = 16384;   // tiles this large look for runs of one tag
 constexpr u32 kSkewRunMin = 512;  // the shortest run copied straight
