@@ -1202,8 +1202,10 @@ __device__ __forceinline__ int warp_bucket_in(const typename K::elem_t *piv, int
 }
 
 // P[Jb][col] = pos for the segments that start between a bucket bp (-1 before
-// a column's first element) and a bucket b >= bp: Jb in (bp/64, b/64].
-__device__ __forceinline__ void count_seg_starts(u32 *P, u32 cols, u32 col, int bp, int b, u32 pos) {
+// a column's first element) and a bucket b >= bp: Jb in (bp/64, b/64].  Out
+// of line: it is rare (a segment spans 64 buckets), and inlined at every
+// element of the unrolled loop it made the kernel wait on instruction fetch.
+static __device__ __noinline__ void count_seg_starts(u32 *P, u32 cols, u32 col, int bp, int b, u32 pos) {
   for (int Jb = (bp + (int)kSkewBkts) / (int)kSkewBkts; Jb <= b / (int)kSkewBkts; ++Jb)
     P[(u64)Jb * cols + col] = pos;
 }
