@@ -519,6 +519,120 @@ def cpu_baseline_wide(sample_log2: int = 21, budget_s: float = 20.0, min_s: floa
                       f"workload's generators), cutoff 16384, single thread", "seconds": round(t, 2)}
 
 
+def bench_huge(args, sq, dist, rank, world, local):
+    """2^31 uint32 keys (uniform, drawn on the device from a seeded generator)
+    with an index payload: a root of 46341 columns whose 46340 pivots a
+    cluster of 8 CTAs sorts and the bucket count reads from global memory.
+    One input copy is sorted per step (restored outside the timed sorts, each
+    sort timed by CUDA events on the launch stream); end to end through
+    sq_sort on page-locked host buffers."""
+    import torch
+
+    from paper_2407_14801_gb300 import dist as D
+
+    dev = torch.device("cuda", local)
+    n = args.huge_n
+    g = torch.Generator(device=dev)
+    g.manual_seed(31 + rank)
+    src = torch.randint(-(1 << 31), 1 << 31, (n,), dtype=torch.int32, device=dev, generator=g)
+    iota = torch.arange(n, dtype=torch.int32, device=dev)
+    keys, vals = src.clone(), iota.clone()
+    stream = torch.cuda.current_stream()
+
+    def restore():
+        keys.copy_(src)
+        vals.copy_(iota)
+        torch.cuda.synchronize()
+
+    for i in range(args.warmup):
+        restore()
+        sq.sort(keys, vals, seed=i, dtype="u32", cutoff=args.cutoff)
+    sq.reset_stats()
+    clocks = make_clocks(local)
+    clocks.start()
+    ms, ok = 0.0, True
+    D.barrier(dist)
+    for i in range(args.steps):
+        restore()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        sq.sort(keys, vals, seed=100 + i, dtype="u32", cutoff=args.cutoff)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms += ev0.elapsed_time(ev1)
+        if i == 0:
+            ok = check_sorted_any(src, keys, vals, "u32")
+    D.barrier(dist)
+    clk = clocks.stop()
+    st_timed = sq.stats()
+    ms_max = D.max_over_ranks(ms, dist, dev)
+    value = world * args.steps * n / (ms_max / 1e3) / 1e9
+
+    def again():
+        for i in range(min(args.steps, 2)):
+            restore()
+            sq.sort(keys, vals, seed=200 + i, dtype="u32", cutoff=args.cutoff)
+
+    st = profiled(sq, again)
+    del keys, vals
+    torch.cuda.empty_cache()
+    workload_name = f"huge_u32_n{n}"
+    roofline = roofline_of(st, workload_name, "a profiling pass over two more sorts after the timed ones")
+    step_frac = (6 * 8 * n) / (ms_max / args.steps / 1e3) / 1e9 / roofline["peak"]
+    e2e = None
+    if not args.no_e2e:
+        hk = torch.empty(n, dtype=torch.int32).pin_memory()
+        hv = torch.empty(n, dtype=torch.int32).pin_memory()
+        tot, reps = 0.0, min(args.steps, 3)
+        for i in range(-1, reps):  # (the first untimed: it grows the device memory pool)
+            hk.copy_(src)
+            hv.copy_(iota)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sq.sort(hk, hv, seed=300 + i, dtype="u32")  # reads and writes the host buffers
+            if i >= 0:
+                tot += time.perf_counter() - t0
+        ok = ok and check_sorted_any(src, hk.to(dev), hv.to(dev), "u32")
+        e2e = {"value": round(reps * n / tot / 1e9, 3), "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+               "d2h_bytes_per_step": 8 * n, "steps": reps, "warmup": 1,
+               "buffers": "pinned host, read by the first pass and written by the last through the device mapping"}
+        del hk, hv
+    return {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": workload_name, "n": n, "key": "uint32 uniform (torch generator, seed 31 + rank)",
+                   "payload": "uint32 original index", "cutoff": args.cutoff or sq.get_cutoff("u32"),
+                   "root": f"{int(n ** 0.5) + 1} columns, pivots sorted by a cluster of 8 CTAs",
+                   "l2": "inputs larger than L2 (restored before each timed sort)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline, "step_hbm_frac_ideal_6wn": round(step_frac, 4), "e2e": e2e,
+        "gpu_launches": int(sum(st_timed["launches"].values())),
+        "rounds_per_step": st_timed["rounds"] / max(1, args.steps), "clocks": clk, "verified": ok,
+    }
+
+
+def cpu_baseline_huge(sample_log2: int = 23, budget_s: float = 25.0, min_s: float = 12.0):
+    """The CPU oracle, single-threaded, on 2^sample_log2-key uniform uint32
+    samples until at least min_s seconds of sorting."""
+    import oracle
+    import workloads as W
+
+    n = 1 << sample_log2
+    k = W.uniform_u32(n, 31)
+    v = W.iota(n)
+    done, t, i = 0, 0.0, 0
+    while t < min_s and t < budget_s:
+        t0 = time.perf_counter()
+        oracle.sort(k, v, seed=1 + i, cutoff=16384)
+        t += time.perf_counter() - t0
+        done += n
+        i += 1
+    return {"value": round(done / t / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{i} sorts of 2^{sample_log2} uniform uint32 keys, cutoff 16384, single thread",
+            "seconds": round(t, 2)}
+
+
 def run_ours(args):
     import torch
 
@@ -543,6 +657,10 @@ def run_ours(args):
         out = bench_batch(args, sq, dist, rank, world, local)
         if rank == 0 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline_batch(args)
+    elif args.workload == "huge":
+        out = bench_huge(args, sq, dist, rank, world, local)
+        if rank == 0 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline_huge()
     elif args.workload == "serve":
         out = bench_serve(args, sq, dist, rank, world, local)
         if rank == 0 and not args.no_cpu_baseline:
@@ -998,7 +1116,7 @@ def main():
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="plain", choices=["plain", "wide", "batch", "serve"])
+    ap.add_argument("--workload", default="plain", choices=["plain", "wide", "batch", "serve", "huge"])
     ap.add_argument("--n", type=int, default=1 << 28)
     ap.add_argument("--cutoff", type=int, default=0)
     ap.add_argument("--variant", default="algorithm1", choices=["algorithm1", "appendix"],
@@ -1011,6 +1129,7 @@ def main():
     ap.add_argument("--batch-no-single", action="store_true",
                     help="skip the per-instance comparison (profiling runs)")
     ap.add_argument("--wide-n", type=int, default=1 << 26, help="keys per array of the wide workload")
+    ap.add_argument("--huge-n", type=int, default=1 << 31, help="keys of the huge workload (uint32)")
     ap.add_argument("--launch-mode", default="auto", choices=["auto", "host", "graph"],
                     help="how recursion rounds are launched (profilers cannot see kernels inside graph loops)")
     ap.add_argument("--dists", default=",".join(DISTS), help="comma-separated subset (profiling runs)")

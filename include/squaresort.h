@@ -98,7 +98,8 @@ typedef struct {
  * whose range holds a single pair (p_{i-1} the predecessor of p_i, or p_0 =
  * the least pair (0, 0)) is copied, not sorted.  Integer keys only (SQ_U32,
  * SQ_U64), a cutoff of at least 8 (so that every node draws m >= 3 samples),
- * and n < sq_max_n(dtype).  Repeated (key, val) pairs are allowed. */
+ * and n < (p + 1)^2 with p = 16384 for SQ_U32, 8192 for SQ_U64 (the samples
+ * are sorted by one CTA).  Repeated (key, val) pairs are allowed. */
 typedef enum { SQ_ALGORITHM1 = 0, SQ_APPENDIX = 1 } sq_variant;
 
 typedef struct {
@@ -142,7 +143,7 @@ typedef struct {
   uint32_t *vals_out;
   const void *pivot_keys;
   const uint32_t *pivot_vals;
-  uint64_t k;                  /* buckets; 1 <= k <= sqrt(sq_max_n(dtype)) */
+  uint64_t k;                  /* buckets; 1 <= k <= p + 1, p = 16384 for SQ_U32, 8192 otherwise */
   uint64_t *bucket_start_out;  /* k+1 entries */
 } sq_skew_buf;
 
@@ -230,8 +231,11 @@ sq_status sq_serve_destroy(sq_server *srv);
 /* Message of the calling thread's last failing call ("" if none). */
 const char *sq_last_error(void);
 
-/* Largest n accepted by sq_sort for `dtype`: (p + 1)^2, p the largest
- * pivot sample one CTA sorts (16384 for SQ_U32, 8192 otherwise). */
+/* Largest n accepted by sq_sort for `dtype`: (p + 1)^2 with p the largest
+ * pivot sample of a node -- for SQ_U32 65535, sorted by a cluster of 8 CTAs,
+ * capped at 2^32 - 1; 8192 otherwise (one CTA).  An SQ_U32 sort above 2^28
+ * has a root with more than 16384 pivots; its bucket count reads them from
+ * global memory. */
 uint64_t sq_max_n(sq_dtype dtype);
 
 /* Largest leaf sorted directly (the largest allowed cutoff): 65536, by a

@@ -224,11 +224,7 @@ const char *sq_last_error(void) { return g_err; }
 
 uint32_t sq_max_leaf(sq_dtype dtype) { return dtype_ok(dtype) ? sq::engine_max_leaf(dtype) : 0; }
 
-uint64_t sq_max_n(sq_dtype dtype) {
-  if (!dtype_ok(dtype)) return 0;
-  const uint64_t m = sq::engine_max_pivots(dtype);
-  return (m + 1) * (m + 1);
-}
+uint64_t sq_max_n(sq_dtype dtype) { return dtype_ok(dtype) ? sq::engine_max_n(dtype) : 0; }
 
 sq_status sq_set_cutoff(sq_dtype dtype, uint32_t cutoff) {
   if (!dtype_ok(dtype)) return fail(SQ_ERR_INVALID, "bad dtype %d", (int)dtype);
@@ -289,9 +285,10 @@ sq_status sq_sort_ex(void *keys, uint32_t *vals, uint64_t n, sq_dtype dtype, uin
     if (dtype == SQ_F32) return fail(SQ_ERR_INVALID, "the appendix variant sorts integer keys");
     if ((opts->cutoff && opts->cutoff < 8) || (!opts->cutoff && cutoff_for(dtype, n) < 8))
       return fail(SQ_ERR_INVALID, "the appendix variant needs a cutoff of at least 8");
-    if (n >= sq_max_n(dtype))
+    const uint64_t p = sq::engine_max_pivots(dtype), vmax = (p + 1) * (p + 1);
+    if (n >= vmax)
       return fail(SQ_ERR_INVALID, "n = %llu: the appendix variant takes n < %llu", (unsigned long long)n,
-                  (unsigned long long)sq_max_n(dtype));
+                  (unsigned long long)vmax);
   }
   if (opts && opts->trace_count) *opts->trace_count = 0;
   cudaStream_t st = (cudaStream_t)stream;

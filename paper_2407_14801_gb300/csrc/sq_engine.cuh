@@ -63,7 +63,11 @@ struct Engine {
   static constexpr u32 kHostExpandCols = 2048;  // roots with this many columns are expanded on the host
 
   static u32 max_leaf() { return class_cap(NCLASS - 1); }
-  static u32 max_pivots() { return LeafCfg<DT>::max_pivots; }
+  static u32 max_pivots() { return LeafCfg<DT>::max_pivots; }  // one CTA's pivot sample
+  // the largest pivot sample of any node (a cluster's, where the key type has one)
+  static u32 max_sample() { return std::max(LeafCfg<DT>::max_pivots, LeafCfg<DT>::max_pivots_big); }
+  // the largest n: (max_sample() + 1)^2, within 32-bit node sizes
+  static u64 max_n() { return std::min<u64>((u64)(max_sample() + 1) * (max_sample() + 1), 0xffffffffull); }
 
   // ---- launch helpers ---------------------------------------------------
   struct Launcher {
@@ -284,6 +288,22 @@ struct Engine {
     if (e == cudaSuccess && maxp > 2048) e = launch_pivots<512, 16, false>(L, cp, ready, 2048, 8192, nsm);
     if constexpr (LeafCfg<DT>::max_pivots > 8192)
       if (e == cudaSuccess && maxp > 8192) e = launch_pivots<1024, 16, false>(L, cp, ready, 8192, 16384, nsm);
+    if constexpr (LeafCfg<DT>::max_pivots_big > 0)
+      if (e == cudaSuccess && maxp > LeafCfg<DT>::max_pivots + 1) e = launch_pivots_cluster(L, cp, ready, nsm);
+    return e;
+  }
+
+  // Samples larger than one CTA sorts: a cluster of 8 CTAs per node.
+  static cudaError_t launch_pivots_cluster(Launcher &L, const Ctx *cp, u32 ready, int nsm) {
+    constexpr int G = 8;
+    const size_t smem = (size_t)Sorter<K, 512, 16, false>::SMEM * sizeof(E);
+    auto kern = k_pivots_cluster<DT>;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    const u32 ncl = std::max<u32>(1, ready == kDev ? (u32)(nsm / G) : std::min<u32>(ready, (u32)(nsm / G)));
+    L.begin(KF_PIVOTS);
+    e = launch_cluster(kern, dim3(G * ncl, 1, 1), 512, smem, G, L.st, cp, ready, (u32)LeafCfg<DT>::max_pivots);
+    L.end();
     return e;
   }
 
@@ -346,10 +366,14 @@ struct Engine {
       } else {
         SQ_TRY(launch_all_pivots(L, cp, ready, kmax, nsm));
       }
-      const size_t smem_count = (size_t)(kmax - 1) * sizeof(E) + (size_t)kmax * 4;
-      SQ_TRY(set_smem(k_count<DT>, smem_count));
+      // nodes with up to kCountSmemPivots pivots: pivots and totals in shared
+      // memory; larger ones (a launch of their own): in global memory
+      const u32 kms = std::min<u32>(kmax, kCountSmemPivots + 1);
+      const size_t smem_count = (size_t)(kms - 1) * sizeof(E) + (size_t)kms * 4;
+      SQ_TRY(set_smem(k_count<DT, false>, smem_count));
       L.begin(KF_COUNT);
-      k_count<DT><<<grid_count, 1024, smem_count, st>>>(cp, ready, kmax);
+      k_count<DT, false><<<grid_count, 1024, smem_count, st>>>(cp, ready, kms);
+      if (kmax - 1 > kCountSmemPivots) k_count<DT, true><<<grid_count, 1024, 0, st>>>(cp, ready, 1u);
       L.end();
       L.local.bytes[KF_COUNT] += (KEY_BYTES + 4) * re;
       SQ_TRY(cudaGetLastError());
@@ -650,17 +674,18 @@ struct Engine {
       total_n += spec.inst[i].n;
       max_n = std::max<u64>(max_n, spec.inst[i].n);
     }
-    const u64 lim = (u64)(max_pivots() + 1) * (max_pivots() + 1);
+    const u64 lim = Engine::max_n();
     if (!spec.skew_only && max_n > lim) {
       snprintf(err, errlen, "n = %llu exceeds the largest supported size %llu for this key type",
                (unsigned long long)max_n, (unsigned long long)lim);
       return 1;
     }
+    const u64 vlim = (u64)(max_pivots() + 1) * (max_pivots() + 1);  // the variant sorts its k samples in one CTA
     for (u32 i = 0; i < ninst && !spec.skew_only; i++)
       if (spec.inst[i].variant &&
-          (spec.inst[i].n >= lim || cutoff_of(i) < 8 || (DT != DT_U32 && DT != DT_U64))) {
+          (spec.inst[i].n >= vlim || cutoff_of(i) < 8 || (DT != DT_U32 && DT != DT_U64))) {
         snprintf(err, errlen, "the appendix variant takes integer keys, n < %llu and a cutoff >= 8",
-                 (unsigned long long)lim);
+                 (unsigned long long)vlim);
         return 1;
       }
     const Plan P = make_plan(total_n, ninst, cutoff, cutoff_max, spec.trace_cap, spec.skew_only, (u32)spec.k, (u32)spec.cols);
@@ -944,8 +969,8 @@ struct Engine {
       // after the host has grown the node pool)
       // every node has k = ceil(sqrt n) <= ceil(sqrt(max_n)); round up to a power of two
       int kb = 1;
-      while ((1u << kb) < std::min<u64>(isqrt_ceil(max_n), max_pivots() + 1)) ++kb;
-      const u32 kmax = std::min<u32>(1u << kb, max_pivots() + 1);
+      while ((1u << kb) < std::min<u64>(isqrt_ceil(max_n), max_sample() + 1)) ++kb;
+      const u32 kmax = std::min<u32>(1u << kb, max_sample() + 1);
       GraphSlot &G = graph_slot(kb);
       rc = graph_prepare(G, dev, nsm, kmax, err, errlen);
       if (rc) return rc;
@@ -1206,7 +1231,7 @@ struct Engine {
         snprintf(err, errlen, "bad admission (slot %u, n %llu)", slot, (unsigned long long)is.n);
         return 1;
       }
-      const u64 lim = (u64)(max_pivots() + 1) * (max_pivots() + 1);
+      const u64 lim = Engine::max_n();
       if (is.n > lim) {
         snprintf(err, errlen, "n = %llu exceeds the largest supported size %llu", (unsigned long long)is.n,
                  (unsigned long long)lim);

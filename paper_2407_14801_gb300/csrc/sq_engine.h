@@ -130,8 +130,13 @@ void api_set_error(const char *msg);
 // Largest leaf (and pivot sample) the engine sorts in one group, per key type.
 uint32_t engine_max_leaf(int dtype);
 
-// Largest pivot sample (k - 1) of one node; bounds n by (max + 1)^2.
+// Largest pivot sample (k - 1) that one CTA sorts: bounds the stand-alone
+// SkewTranspose's k and the appendix variant's n, (max + 1)^2.
 uint32_t engine_max_pivots(int dtype);
+
+// Largest n of a sort (larger pivot samples sorted by a cluster of CTAs where
+// the key type has that path).
+uint64_t engine_max_n(int dtype);
 
 // Global statistics (all engines, all threads), and kernel timing switch.
 void engine_stats_get(EngineStats *out);

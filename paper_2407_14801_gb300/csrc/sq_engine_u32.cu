@@ -203,6 +203,11 @@ uint32_t engine_max_pivots(int dtype) {
                          : (dtype == DT_U64 ? Engine<DT_U64>::max_pivots() : Engine<DT_F32>::max_pivots());
 }
 
+uint64_t engine_max_n(int dtype) {
+  return dtype == DT_U32 ? Engine<DT_U32>::max_n()
+                         : (dtype == DT_U64 ? Engine<DT_U64>::max_n() : Engine<DT_F32>::max_n());
+}
+
 uint32_t engine_max_leaf(int dtype) {
   return dtype == DT_U32 ? Engine<DT_U32>::max_leaf()
                          : (dtype == DT_U64 ? Engine<DT_U64>::max_leaf() : Engine<DT_F32>::max_leaf());

@@ -34,20 +34,26 @@ struct LeafCfg;
 // samples use the single-CTA sorters only.
 template <int DT>
 struct LeafCfg;
+// max_pivots: the largest sample one CTA sorts; max_pivots_big: the largest
+// that a cluster of 8 CTAs sorts (k_pivots_cluster; uint32 keys only, whose
+// sort then reaches n = 2^32 - 1), 0 for none.
 template <>
 struct LeafCfg<DT_U32> {
   static constexpr int nclass = kLeafClasses;
   static constexpr u32 max_pivots = 16384;
+  static constexpr u32 max_pivots_big = 65535;
 };
 template <>
 struct LeafCfg<DT_F32> {
   static constexpr int nclass = kLeafClasses;
   static constexpr u32 max_pivots = 8192;
+  static constexpr u32 max_pivots_big = 0;
 };
 template <>
 struct LeafCfg<DT_U64> {
   static constexpr int nclass = kLeafClasses;
   static constexpr u32 max_pivots = 8192;
+  static constexpr u32 max_pivots_big = 0;
 };
 constexpr u32 kClusterPart = 8192;  // elements per CTA of the cluster classes
 __host__ __device__ __forceinline__ u32 class_cap(int c) {
@@ -1149,6 +1155,128 @@ __global__ void __launch_bounds__(WARP ? 256 : T) k_pivots(const Ctx *__restrict
   }
 }
 
+// Pivot step of nodes whose sample is larger than one CTA sorts (k - 1 in
+// (max_pivots, 8 * 8192]): one cluster of 8 CTAs of 512 x 16 per node.  CTA
+// rank draws sample positions [rank*8192, rank*8192 + 8192) and sorts them,
+// the cluster's merge rounds order the whole sample, and Algorithm 1's
+// checks (no two drawn elements equal, the smallest above min(D)) and
+// redraws run across the cluster, the element after a CTA's part and the
+// cluster's verdict read through distributed shared memory.  Besides pk / pv
+// the pivots go to the node's pe section as whole elements, where the count
+// reads them.
+template <int DT>
+__global__ void __launch_bounds__(512, 1) k_pivots_cluster(const Ctx *__restrict__ cp, u32 ready_count, u32 pmin) {
+  const Ctx &c = *cp;
+  if (ready_count == kDev) ready_count = min(c.cnt_cur->ready, c.ready_cap);
+  typedef KT<DT> K;
+  constexpr int T = 512, R = 16, G = 8;
+  typedef ClusterSorter<K, T, R, G> CS;
+  typedef typename K::elem_t E;
+  typedef typename K::key_t key_t;
+  namespace cg = cooperative_groups;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  E *s = reinterpret_cast<E *>(smem_raw);
+  __shared__ E s_first[T];  // every thread's first sorted element
+  __shared__ E s_red[T / 32];
+  __shared__ E s_min;
+  __shared__ int s_bad;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const u32 ncl = gridDim.x / G;
+  for (u32 ri = blockIdx.x / G; ri < ready_count; ri += ncl) {  // (the same node for the whole cluster)
+    Node *nd = &c.nodes[c.ready_cur[ri]];
+    const u32 np = nd->k - 1;  // pivots to draw
+    const Inst I = c.inst[nd->inst];
+    if (np <= pmin || I.variant == VAR_APPENDIX) continue;
+    const MetaLayout ML = meta_layout(nd->k, nd->cols, nd->ncb, nd->nkb, K::key_words);
+    if (nd->meta + ML.total > c.meta_cap) continue;
+    const key_t *dk = (const key_t *)I.dkeys + nd->off;
+    const u32 *dv = I.dvals + nd->off;
+    const u64 n = nd->n;
+    // min(D) over the column heads: CTA rank takes every G-th block of T columns
+    E mn = K::top();
+    for (u32 i = (u32)rank * T + tid; i < nd->cols; i += G * T) {
+      const u64 p = (u64)i * nd->rows;
+      if (p < n) {
+        const E e = K::make(dk[p], dv[p]);
+        if (K::lt(e, mn)) mn = e;
+      }
+    }
+    mn = warp_min<K>(mn);
+    if (lane == 0) s_red[warp] = mn;
+    __syncthreads();
+    if (tid == 0) {
+      E v = s_red[0];
+      for (int w = 1; w < T / 32; w++)
+        if (K::lt(s_red[w], v)) v = s_red[w];
+      s_min = v;
+    }
+    cl.sync();
+    if (rank == 0 && tid == 0)
+      for (int r = 1; r < G; r++) {
+        const E o = *cl.map_shared_rank(&s_min, r);
+        if (K::lt(o, mn)) mn = o;
+      }
+    if (rank == 0 && tid == 0) mn = K::lt(s_min, mn) ? s_min : mn;
+    key_t *pk = reinterpret_cast<key_t *>(c.meta + nd->meta + ML.pk);
+    u32 *pv = c.meta + nd->meta + ML.pv;
+    E *pe = reinterpret_cast<E *>(c.meta + nd->meta + ML.pe);
+    const u32 q0 = (u32)rank * CS::NC + (u32)tid * R;  // this thread's first sample position
+    bool done = false;
+    for (int a = 0; a < kMaxAttempts && !done; a++) {
+      const u64 sa = attempt_seed(nd->hash, (u64)a);
+      E x[R];
+#pragma unroll
+      for (int q = 0; q < R; q++) {
+        const u32 r = q0 + q;
+        if (r < np) {
+          const u64 t = __umul64hi(draw(sa, r), n);
+          x[q] = K::make(dk[t], dv[t]);
+        } else {
+          x[q] = K::top();
+        }
+      }
+      CS::sort(x, s, tid, (int)np);
+      bool bad = false;
+#pragma unroll
+      for (int q = 0; q + 1 < R; q++)
+        if (q0 + q + 1 < np && K::eq(x[q], x[q + 1])) bad = true;
+      s_first[tid] = x[0];
+      cl.sync();  // (every CTA's firsts written; every merge-round read of s done)
+      if (q0 + R < np) {
+        const E nx = tid + 1 < T ? s_first[tid + 1] : *cl.map_shared_rank(&s_first[0], rank + 1);
+        if (K::eq(x[R - 1], nx)) bad = true;
+      }
+      if (rank == 0 && tid == 0 && K::eq(x[0], mn)) bad = true;
+      const int any = __syncthreads_or(bad);
+      if (tid == 0) s_bad = any;
+      cl.sync();
+      int cbad = 0;
+      for (int r = 0; r < G; r++) cbad |= *cl.map_shared_rank(&s_bad, r);
+      cl.sync();  // the verdicts and firsts are read before the next attempt rewrites them
+      if (!cbad) {
+#pragma unroll
+        for (int q = 0; q < R; q++) {
+          const u32 r = q0 + q;
+          if (r < np) {
+            pk[r] = K::key(x[q]);
+            pv[r] = K::val(x[q]);
+            pe[r] = x[q];
+          }
+        }
+        if (rank == 0 && tid == 0) {
+          nd->attempts = (u32)a + 1;
+          trace_node(c, nd, (u32)a + 1);
+        }
+        done = true;
+      }
+    }
+    if (!done && rank == 0 && tid == 0) atomicOr(&c.status->error, ERRB_ATTEMPTS);
+    cl.sync();  // the node is finished by every CTA before the cluster takes the next
+  }
+}
+
 // Exclusive prefix sum over a warp (and the warp total).
 __device__ __forceinline__ u32 warp_excl_scan(u32 v, u32 &total) {
   const int lane = threadIdx.x & 31;
@@ -1176,7 +1304,11 @@ __device__ __forceinline__ u32 warp_excl_scan(u32 v, u32 &total) {
 // T[I][j], per column the start P[Jb][i] of every kSkewBkts-bucket segment
 // (the first position whose bucket is at least Jb*kSkewBkts; the column's
 // length past its last bucket), and every element's tag (its bucket within
-// its segment) for the SkewTranspose.
+// its segment) for the SkewTranspose.  GP: the launch for nodes with more
+// than kCountSmemPivots pivots, read from the node's pe section in global
+// memory (cached in L1/L2), the bucket totals added straight into the
+// block's row of T; the other launch keeps pivots and totals in shared
+// memory.  Each launch takes only its own nodes' units.
 
 constexpr int kCountE = 8;     // count: consecutive elements a lane
 constexpr int kCountStep = 8;  // count: pivots stepped over one by one before a binary search
@@ -1210,7 +1342,7 @@ static __device__ __noinline__ void count_seg_starts(u32 *P, u32 cols, u32 col, 
     P[(u64)Jb * cols + col] = pos;
 }
 
-template <int DT>
+template <int DT, bool GP>
 __global__ void __launch_bounds__(1024) k_count(const Ctx *__restrict__ cp, u32 ready_count, u32 kmax) {
   const Ctx &c = *cp;
   if (ready_count == kDev) ready_count = min(c.cnt_cur->ready, c.ready_cap);
@@ -1221,26 +1353,32 @@ __global__ void __launch_bounds__(1024) k_count(const Ctx *__restrict__ cp, u32 
   constexpr u32 CH = 32 * EL;  // elements of a warp chunk
   static_assert(EL % 4 == 0, "128-bit payload loads and word tag stores take 4 elements at a time");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  E *piv = reinterpret_cast<E *>(smem_raw);
-  u32 *hist = reinterpret_cast<u32 *>(piv + (kmax > 1 ? kmax - 1 : 1));
+  E *piv_s = reinterpret_cast<E *>(smem_raw);
+  u32 *hist_s = reinterpret_cast<u32 *>(piv_s + (kmax > 1 ? kmax - 1 : 1));
   __shared__ u32 s_u, s_ri;
   __shared__ u32 s_cpre[kCountCols + 1];  // chunks before each column of the block
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int NT = blockDim.x, NW = NT >> 5;
   u32 cur = kNone;
   for (;;) {
-    grab_item(c, &c.status->cur_count, c.status->units, 0, ready_count, &s_u, &s_ri);
+    grab_item(c, GP ? &c.status->cur_count_big : &c.status->cur_count, c.status->units, 0, ready_count, &s_u,
+              &s_ri);
     __syncthreads();
     const u32 u = s_u;
     if (u >= c.status->units) break;
     const u32 id = c.ready_cur[s_ri];
     const Node nd = c.nodes[id];
+    __syncthreads();  // (s_u / s_ri are read everywhere before warp 0 may take the next unit)
+    if ((nd.k - 1 > kCountSmemPivots) != GP) continue;  // the other launch's node
     const int np = (int)nd.k - 1;
     const MetaLayout ML = meta_layout(nd.k, nd.cols, nd.ncb, nd.nkb, K::key_words);
     u32 *meta = c.meta + nd.meta;
-    if (id != cur) {
+    const u32 Iblk = u - nd.unit_base;
+    const E *piv = GP ? reinterpret_cast<const E *>(meta + ML.pe) : piv_s;
+    u32 *hist = GP ? meta + ML.T + (u64)Iblk * nd.k : hist_s;
+    if (!GP && id != cur) {
       const key_t *pk = reinterpret_cast<const key_t *>(meta + ML.pk);
-      for (int j = tid; j < np; j += NT) piv[j] = K::make(pk[j], meta[ML.pv + j]);
+      for (int j = tid; j < np; j += NT) piv_s[j] = K::make(pk[j], meta[ML.pv + j]);
       cur = id;
     }
     for (u32 j = tid; j < nd.k; j += NT) hist[j] = 0;
@@ -1251,7 +1389,6 @@ __global__ void __launch_bounds__(1024) k_count(const Ctx *__restrict__ cp, u32 
     u32 *P = meta + ML.P;
     const u32 rows = nd.rows, n = nd.n, cols = nd.cols, nkb = nd.nkb;
     const bool le = I.variant == VAR_APPENDIX;  // buckets bounded above by "<="
-    const u32 Iblk = u - nd.unit_base;
     const u32 i0 = Iblk * kCountCols;
     const u32 nc = min(cols, i0 + kCountCols) - i0;
     if (warp == 0) {
@@ -1401,9 +1538,11 @@ __global__ void __launch_bounds__(1024) k_count(const Ctx *__restrict__ cp, u32 
       lo = hn;
     }
     __syncthreads();
-    u32 *T = meta + ML.T;
-    for (u32 j = tid; j < nd.k; j += NT) T[(u64)Iblk * nd.k + j] = hist[j];
-    __syncthreads();
+    if (!GP) {
+      u32 *T = meta + ML.T;
+      for (u32 j = tid; j < nd.k; j += NT) T[(u64)Iblk * nd.k + j] = hist_s[j];
+      __syncthreads();
+    }
   }
 }
 

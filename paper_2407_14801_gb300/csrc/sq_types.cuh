@@ -313,8 +313,9 @@ struct Status {
   u32 cur_count, cur_scan, cur_skew, cur_expand, cur_ebkt, cur_fix, fix_count;
   u32 cur_leaf[kLeafClasses];
   u32 runs_count, runs_cursor;  // this round's run copies (RunCopy list)
+  u32 cur_count_big;             // the count's units of nodes whose pivots stay in global memory
 };
-constexpr int kRoundCursors = 7 + kLeafClasses + 2;  // Status words from cur_count on, zeroed every round
+constexpr int kRoundCursors = 7 + kLeafClasses + 3;  // Status words from cur_count on, zeroed every round
 
 // One column's piece of a run of one bucket tag in a big SkewTranspose tile:
 // n elements from D at src to A at dst (element offsets in the instance).
@@ -377,8 +378,13 @@ struct Ctx {
 // T[j][I] block totals -> exclusive prefixes (k * ncb), P[Jb][i] segment
 // starts (nkb * cols), bucket starts b[0..k] (k+1).
 struct MetaLayout {
-  u64 pk, pv, T, P, b, total;
+  u64 pk, pv, T, P, b, pe, total;
 };
+
+// Pivots that the count keeps in shared memory (with its k bucket totals):
+// larger nodes keep them, as whole elements, in their metadata (section pe)
+// and the count reads them from there.
+constexpr u32 kCountSmemPivots = 16384;
 
 __host__ __device__ __forceinline__ u64 align4(u64 x) { return (x + 3) & ~3ull; }
 
@@ -395,6 +401,8 @@ __host__ __device__ __forceinline__ MetaLayout meta_layout(u32 k, u32 cols, u32 
   p += align4((u64)nkb * cols);
   L.b = p;
   p += align4((u64)k + 1);
+  L.pe = p;
+  if (k - 1 > kCountSmemPivots) p += align4((u64)(k - 1) * 4);  // (room for 16-byte elements)
   L.total = p;
   return L;
 }

@@ -43,7 +43,8 @@ def test_library_exports_every_declared_symbol(sq):
 
 def test_limits(sq):
     assert sq.max_leaf("u32") == 65536 and sq.max_leaf("u64") == 65536 and sq.max_leaf("f32") == 65536
-    assert sq.max_n("u32") == 16385 ** 2 >= 1 << 28
+    assert sq.max_n("u32") == 2**32 - 1  # (65535 + 1)^2 capped to 32-bit sizes: cluster-sorted pivot samples
+    assert sq.max_n("f32") == 8193 ** 2
     assert sq.max_n("u64") == 8193 ** 2 >= 1 << 26
 
 
@@ -67,7 +68,7 @@ def test_rejects_bad_arguments_without_a_device(sq):
 
 def test_appendix_variant_refusals_without_a_device(sq):
     """The variant takes integer keys, a cutoff of at least 8 and n below
-    sq_max_n; the checks come before any device work."""
+    (16384 + 1)^2 for uint32 keys; the checks come before any device work."""
     L = sq.lib()
 
     def ex(dtype, n, cutoff, variant):
@@ -77,7 +78,7 @@ def test_appendix_variant_refusals_without_a_device(sq):
     assert ex(2, 10, 16, 1) == 1 and b"integer" in L.sq_last_error()  # SQ_F32
     assert ex(0, 10, 7, 1) == 1 and b"cutoff" in L.sq_last_error()
     assert ex(0, 10, 16, 2) == 1 and b"variant" in L.sq_last_error()
-    assert ex(0, sq.max_n("u32"), 16, 1) == 1 and b"appendix" in L.sq_last_error()
+    assert ex(0, 16385**2, 16, 1) == 1 and b"appendix" in L.sq_last_error()
     assert ex(1, sq.max_n("u64"), 16, 1) == 1
     assert sq.VARIANTS == {"algorithm1": 0, "appendix": 1}
 
