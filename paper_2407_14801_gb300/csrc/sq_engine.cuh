@@ -480,8 +480,8 @@ struct Engine {
   };
   // One graph per bound on the nodes' k (a power of two, so that the count
   // kernel's shared memory and the pivot-sort launches fit the run).
-  static GraphSlot &graph_slot(int kb) {
-    static thread_local GraphSlot s[16];
+  static GraphSlot &graph_slot(int kb) {  // kb <= 16: k <= max_sample() + 1 <= 2^16
+    static thread_local GraphSlot s[17];
     return s[kb];
   }
 

@@ -11,6 +11,8 @@ of 8 CTAs, the bucket count reading its pivots from global memory.
   permutation, every key with its payload).
 - n = 2^31 from page-locked host buffers (the first pass reads them, the last
   writes them): the output by the same properties.
+- n = 2^31 with every round in one CUDA-graph launch (the graph sized for
+  k up to 2^16).
 """
 import numpy as np
 import pytest
@@ -88,3 +90,19 @@ def test_u32_2e31_from_pinned_host_memory(sq):
     out_v = hv.cuda()
     del hk, hv
     check_unique_result(src, out_k, out_v)
+
+
+def test_u32_2e31_graph_launch_mode(sq):
+    n = 1 << 31
+    g = torch.Generator(device="cuda")
+    g.manual_seed(32)
+    src = torch.randint(-(1 << 31), 1 << 31, (n,), dtype=torch.int32, device="cuda", generator=g)
+    keys = src.clone()
+    vals = torch.arange(n, dtype=torch.int32, device="cuda")
+    sq.set_launch_mode("graph")
+    try:
+        sq.sort(keys, vals, seed=6, dtype="u32")
+        sq.sync()
+    finally:
+        sq.set_launch_mode("auto")
+    check_unique_result(src, keys, vals)
