@@ -7,8 +7,8 @@
 //   k_pivots        draws, sorts and checks those nodes' pivot samples;
 //   k_count         one pass over each sorted column: bucket totals per block
 //                   of columns and the start of every 64-bucket segment
-//                   (Section 2.2, "scan of the column simultaneously with the
-//                   scan of the pivots");
+//                   (Section 2.2: a sorted column and the sorted pivots are
+//                   walked together, a merge);
 //   k_scan/k_bstart prefix sums: bucket starts and per-block offsets;
 //   k_skew          SkewTranspose (Algorithm 2 / 3) as a tiled stable
 //                   partition staged in shared memory;
