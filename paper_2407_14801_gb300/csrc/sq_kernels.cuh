@@ -1161,7 +1161,7 @@ __global__ void __launch_bounds__(WARP ? 256 : T) k_pivots(const Ctx *__restrict
 // the cluster's merge rounds order the whole sample, and Algorithm 1's
 // checks (no two drawn elements equal, the smallest above min(D)) and
 // redraws run across the cluster, the element after a CTA's part and the
-// cluster's verdict read through distributed shared memory.  Besides pk / pv
+// cluster's outcome read through distributed shared memory.  Besides pk / pv
 // the pivots go to the node's pe section as whole elements, where the count
 // reads them.
 template <int DT>
@@ -1254,7 +1254,7 @@ __global__ void __launch_bounds__(512, 1) k_pivots_cluster(const Ctx *__restrict
       cl.sync();
       int cbad = 0;
       for (int r = 0; r < G; r++) cbad |= *cl.map_shared_rank(&s_bad, r);
-      cl.sync();  // the verdicts and firsts are read before the next attempt rewrites them
+      cl.sync();  // the outcomes and firsts are read before the next attempt rewrites them
       if (!cbad) {
 #pragma unroll
         for (int q = 0; q < R; q++) {
