@@ -31,7 +31,7 @@
 
 namespace sq {
 
-template <class K, int T, int R, int BITS = 5, int G = 4>
+template <class K, int T, int R, int BITS = 5, int G = 2>
 struct RadixLeaf {
   typedef Sorter<K, T, R, false> S;
   typedef typename K::elem_t E;
