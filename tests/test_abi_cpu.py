@@ -83,6 +83,19 @@ def test_appendix_variant_refusals_without_a_device(sq):
     assert sq.VARIANTS == {"algorithm1": 0, "appendix": 1}
 
 
+def test_skew_transpose_keeps_the_one_cta_pivot_limit(sq):
+    """Sorts of uint32 keys reach 2^32 - 1 (cluster-sorted pivot samples),
+    but the stand-alone SkewTranspose takes k up to 16385 buckets for uint32
+    and 8193 otherwise; the check comes before any device work."""
+    L = sq.lib()
+    dummy = ctypes.c_void_p(8)
+    for dtype, kmax in ((0, 16385), (1, 8193), (2, 8193)):
+        buf = sq.SkewBuf(dtype, 4, dummy, dummy, dummy, dummy, dummy, dummy, kmax + 1, dummy)
+        assert L.sq_skew_transpose(ctypes.byref(buf), 2, 2, None) == 1
+        assert b"k = " in L.sq_last_error()
+        assert L.sq_skew_transpose_noalloc(ctypes.byref(buf), 2, 2, None) == 1
+
+
 def test_launch_mode_without_a_device(sq):
     L = sq.lib()
     assert L.sq_get_launch_mode() == 2  # auto
